@@ -1,0 +1,416 @@
+"""Benchmark of the GB300 WECT library (one JSON line on rank 0).
+
+Default workload: the WECT of the cubical complex of a 128^3 voxel volume (smoothed Gaussian
+random field quantised to u8), d = 256 Fibonacci directions, T = 128 thresholds over
+[-sqrt3, sqrt3].  One step = set the vertex weights (device copy + check) and compute the
+transform: every row of the hot path (weights, threshold table, fused stencil scatter,
+prefix scan).  The metric is simplex.direction evaluations per second: (cells of the complex)
+x d per step, summed over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank transforms its own volume (the path
+partitions into independent complexes, no collective on the data path); timing is the max
+over ranks.  --impl reference times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "WECT simplex·direction evals/s on 1 GB300; % HBM peak; fwd+bwd/fwd time"
+UNIT = "simplex·direction evals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            j = json.load(fh)
+        return j, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+
+
+def oracle_sample(wl, ndirs: int):
+    """Time the CPU oracle (single thread, as it stands) on ndirs directions of the workload."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    O.build()
+    vw = wl.grid.ravel().astype(np.int64)
+    t0 = time.perf_counter()
+    O.wect_cubical(wl.dims, vw, wl.dirs[:ndirs], wl.T, wl.lo, wl.hi)
+    return time.perf_counter() - t0
+
+
+def cells_of(dims):
+    c = 1
+    for L in dims:
+        c *= 2 * L - 1
+    return c
+
+
+# ------------------------------------------------------------------ traffic from the committed profile
+
+
+def _traffic_per_launch():
+    """DRAM bytes per launch of the forward kernel from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2511_03909_gb300", "csrc", "wect_cubical.cu")
+    prof = os.path.join(ROOT, "profiles", "cubical_fwd_voxel3d_128.md")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for ln in open(prof):
+            if ln.startswith("traffic_bytes_per_launch:"):
+                _, val, _, sha = ln.split()
+                return float(val) if sha == h else None
+    except Exception:
+        return None
+    return None
+
+
+# ------------------------------------------------------------------ reference arm
+
+
+def run_reference(args):
+    ws, rank, local = _dist_env()
+    if rank != 0:
+        return 0
+    import synthetic as S
+
+    wl = S.voxel3d_128()
+    cells = cells_of(wl.dims)
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1)
+    ts = [oracle_sample(wl, 1) for _ in range(args.steps)]
+    sec = sum(ts) / len(ts)
+    val = cells / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl.name, "cells": cells, "d": len(wl.dirs), "T": wl.T,
+                   "sample": "1 of 256 directions per step"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 direction of the 128^3 workload per step, single-threaded C oracle"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2511_03909_gb300 as P
+    import synthetic as S
+
+    ws, rank, local = _dist_env()
+    dist = ws > 1
+    if dist:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P._build.build()
+    P.load()
+
+    wl = S.voxel3d_128()
+    cells = cells_of(wl.dims)
+    d, T = len(wl.dirs), wl.T
+    evals_per_step = cells * d
+    grid_h = torch.from_numpy(wl.grid).pin_memory()
+    dirs_h = torch.from_numpy(wl.dirs).pin_memory()
+    grid_d = grid_h.to(dev)
+    dirs_d = dirs_h.to(dev)
+    out = torch.empty((d, T), dtype=torch.int64, device=dev)
+    out_h = torch.empty((d, T), dtype=torch.int64).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    cx = P.CubicalComplex(grid_d)
+
+    def step():
+        cx.set_weights(grid_d)
+        cx.wect(dirs_d, T, wl.lo, wl.hi, out=out)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    barrier()
+
+    # ---- device-resident timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    P.profile_enable(True)
+    l0 = P.launch_count()
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                    # L2 flush outside the timed events
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = P.launch_count() - l0
+    kern_ms, kern_n = P.profile_read()
+    P.profile_enable(False)
+    ck = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = evals_per_step * ws / (ms / 1e3)
+
+    # ---- end to end through the public API, host buffers, copies inside the timed region
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e2e_ev[i][0].record()
+        grid_d.copy_(grid_h, non_blocking=True)
+        dirs_d.copy_(dirs_h, non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
+        e2e_ev[i][1].record()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = evals_per_step * ws / (e2e_ms / 1e3)
+
+    # ---- correctness of the timed output on sampled directions (device result vs oracle)
+    # is covered by the GPU tests; here only the invariant last column is checked.
+    o = out.cpu().numpy()
+    assert np.all(o[:, -1] == o[0, -1]), "last column must be the weighted Euler characteristic"
+
+    if rank != 0:
+        if dist:
+            tdist.destroy_process_group()
+        return 0
+
+    peaks, src = _peaks()
+    # roofline of the dominant kernel (the fused stencil scatter): issue-bound arithmetic.
+    # Algorithmic work per vertex.direction update: 3 lane operations (the height fma, the
+    # rounding to a bin, the integer add into the histogram); peak lane-op rate = 152 SMs x 128
+    # lanes x the SM clock.
+    nv = int(np.prod(wl.dims))
+    kernel_ms = kern_ms / max(kern_n, 1)
+    ops = 3.0 * nv * d
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = 152 * 128 * sm_mhz * 1e6
+    achieved = ops / (kernel_ms / 1e3)
+    hbm_bytes = nv * 1 + d * T * 8 + d * 3 * 8
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak_ops, "traffic": _traffic_per_launch(),
+            "kernel": "cubical_fwd_kernel", "kernel_ms": kernel_ms,
+            "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({src} sm_max_mhz)",
+            "hbm_gbs": hbm_bytes / (kernel_ms / 1e3) / 1e9,
+            "hbm_frac": hbm_bytes / (kernel_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+
+    # CPU baseline: the oracle on a bounded sample (a few directions) of the same workload
+    cpu = None
+    if not args.no_cpu_baseline:
+        ndirs = 3
+        sec = oracle_sample(wl, ndirs)
+        cpu = {"value": cells * ndirs / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ndirs} of {d} directions of the 128^3 workload, single-threaded C oracle ({sec:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "cells": cells, "vertices": nv, "d": d, "T": T,
+                   "range": [wl.lo, wl.hi], "weights": "u8 smoothed Gaussian field (seed 2)",
+                   "l2": "flushed between steps (256 MiB device write outside the timed events)",
+                   "parallelism": f"replicas x{ws} (one volume per GPU)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.numel() + dirs_h.numel() * 8),
+                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "wall_s": t_wall,
+    }
+    if args.extras:
+        line["extras"] = extras(P, S, dev)
+    print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def extras(P, S, dev):
+    """Side measurements named by the metric: batched vs per-image loop, forward+backward vs
+    forward (differentiation workload), both timed with CUDA events."""
+    import torch
+
+    res = {}
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # batched images: 4096 2D blob images, d=64, T=64
+    wl = S.image_batch()
+    dirs = torch.from_numpy(wl.dirs).to(dev)
+    b = P.CubicalBatch([torch.from_numpy(x).to(dev) for x in wl.grids])
+    out = torch.empty((len(wl.grids), 64, 64), dtype=torch.int64, device=dev)
+    t_batch = timed(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out))
+    t_loop = timed(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out, loop=True), reps=2)
+    cells = sum((2 * x.shape[0] - 1) * (2 * x.shape[1] - 1) for x in wl.grids)
+    res["images2d_4096"] = {"batched_ms": t_batch, "loop_ms": t_loop, "speedup": t_loop / t_batch,
+                            "evals_per_s": cells * 64 / (t_batch / 1e3)}
+    del b, out
+    # differentiation: 256 volumes 64^3 f32, d=128, T=128, MSE against a target batch
+    wv = S.volume_batch_diff()
+    dirs = torch.from_numpy(wv.dirs).to(dev)
+    flat = torch.from_numpy(wv.grids.reshape(-1)).to(dev)
+    bt = P.CubicalBatch(flat=torch.from_numpy(wv.target.reshape(-1)).to(dev), dims=[wv.dims] * len(wv.grids),
+                        frac_bits=24)
+    Bt = bt.wect(dirs, wv.T, wv.lo, wv.hi).to(torch.float64) * 2.0 ** -24
+    del bt
+    bb = P.CubicalBatch(flat=flat, dims=[wv.dims] * len(wv.grids), frac_bits=24)
+    w = flat.clone().requires_grad_(True)
+
+    def fwd():
+        with torch.no_grad():
+            W = P.WECTFunction.apply(bb, w, dirs, wv.T, wv.lo, wv.hi)
+            return ((W - Bt) ** 2).mean()
+
+    def fwd_bwd():
+        w.grad = None
+        W = P.WECTFunction.apply(bb, w, dirs, wv.T, wv.lo, wv.hi)
+        loss = ((W - Bt) ** 2).mean()
+        loss.backward()
+
+    tf = timed(fwd)
+    tfb = timed(fwd_bwd)
+    cells = len(wv.grids) * cells_of(wv.dims)
+    res["volumes3d_256x64^3"] = {"fwd_ms": tf, "fwd_bwd_ms": tfb, "ratio": tfb / tf,
+                                 "fwd_evals_per_s": cells * 128 / (tf / 1e3)}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", action="store_true", help="also time the batched and differentiation workloads")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

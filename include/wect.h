@@ -1,0 +1,259 @@
+/*
+ * wect.h -- C ABI of the GB300 (sm_103a) weighted Euler characteristic transform library.
+ *
+ * The library computes, for a weighted geometric simplicial or cubical complex (K, w), a
+ * set of d directions s_p and T thresholds beta[0..T-1],
+ *
+ *     W[p][q] = sum over cells s of K with bin(max_{v in s} h_p(v)) <= q of (-1)^dim(s) w(s),
+ *
+ * the discretised weighted Euler characteristic transform (Definition "wect"; Algorithm 1
+ * with the height filters of Example "ex:wect"); ecf_compute does the same for one caller
+ * supplied vertex filter (Eq. "ecf", Remark "which-ecf").
+ *
+ * Numerical contract (identical on every call, independent of launch shape):
+ *   heights      h = x[n-1]*s[n-1], then h = fma(x[c], s[c], h) for c = n-2..0, float64;
+ *   thresholds   step = (hi-lo)/(T-1), beta[q] = lo + q*step (float64, each op rounded);
+ *   bins         bin(t) = #{q in [0, T-2] : beta[q] < t}  (exact; values above hi fall in
+ *                T-1, so the last column is the weighted Euler characteristic of K);
+ *   weights      int64 fixed point: u8 as is, f32 as rint(w * 2^frac_bits); the weight of a
+ *                cell of dimension >= 1 is the max of its vertex weights (Figure 1) unless
+ *                explicit simplex weights are given;
+ *   output       int64 in the same fixed-point units, exact (order-independent sums).
+ * Grid coordinates of a cubical complex are x_a(i) = (2i - (L_a-1)) / (L_a-1) (0 when
+ * L_a = 1); axis 0 is the fastest-varying axis of every grid array.
+ *
+ * Conventions.
+ *   - Pointers marked (dev) are CUDA device pointers; (host) are host pointers.  The
+ *     caller owns every pointer it passes; create calls copy what they keep, so inputs may
+ *     be freed after they return.  Outputs must not alias inputs.
+ *   - Every compute call is asynchronous and ordered on the given stream (a cudaStream_t;
+ *     NULL is the legacy default stream).  Create calls synchronise the stream once.
+ *   - Every call returns a wect_status; no C++ exception crosses the ABI.  On an argument
+ *     error nothing is launched and outputs are untouched.  wect_last_error() returns a
+ *     thread-local description of the last failure.
+ *   - Device-side conditions that cannot be checked before launch (weights that outgrow the
+ *     accumulator chosen at create time, a bounded wait that ran out) set a per-complex
+ *     status word, read and cleared by wect_complex_device_status().
+ */
+#ifndef WECT_H
+#define WECT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WECT_API __attribute__((visibility("default")))
+#else
+#define WECT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wect_complex_s *wect_complex;   /* opaque, owned by the library */
+typedef struct wect_batch_s *wect_batch;       /* opaque, owned by the library */
+typedef void *wect_stream;                     /* a cudaStream_t */
+
+typedef enum {
+    WECT_OK = 0,
+    WECT_ERR_INVALID_ARG = 1,   /* bad sizes, T < 2, lo > hi, NaN/Inf input, index out of range */
+    WECT_ERR_OUT_OF_MEMORY = 2, /* a device allocation failed */
+    WECT_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in wect_last_error) */
+    WECT_ERR_OVERFLOW = 4,      /* weights too large for exact int64 accumulation */
+    WECT_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    WECT_ERR_UNSUPPORTED = 6    /* a valid request this build does not implement */
+} wect_status;
+
+typedef enum {
+    WECT_W_U8 = 0,        /* uint8 vertex weights, used as integers */
+    WECT_W_I64_FIXED = 1, /* int64 vertex weights already in fixed point */
+    WECT_W_F32 = 2,       /* float32 vertex weights, converted to rint(w * 2^frac_bits) */
+    WECT_W_ONE = 3        /* unweighted: every cell has weight 1 (weights pointer ignored) */
+} wect_wtype;
+
+typedef enum {
+    WECT_SW_MAX_OF_VERTICES = 0, /* w(s) = max of the vertex weights of s (Figure 1) */
+    WECT_SW_EXPLICIT = 1         /* per-simplex int64 fixed-point weights supplied */
+} wect_simplex_weight_mode;
+
+/* ---------------------------------------------------------------- complexes */
+
+/*
+ * Cubical complex of a full n-dimensional grid (n = 1, 2, 3): every vertex, edge, square and
+ * cube of the grid (Section 2: the method applies to cubical complexes; cells are boxes of the
+ * grid with one corner per sub-mask of their extent).
+ *   n               ambient dimension, 1..3
+ *   dims (host)     [n] axis lengths, dims[0] = fastest axis, each >= 1, product < 2^31
+ *   vertex_weights  (dev) [prod dims] of the type given by wtype (ignored for WECT_W_ONE)
+ *   frac_bits       fractional bits for WECT_W_F32 (0..40), else ignored
+ * Errors: INVALID_ARG for bad sizes or non-finite f32 weights; OVERFLOW when a cell's signed
+ * contribution 2^n * max|w| does not fit 31 bits.
+ */
+WECT_API wect_status wect_complex_create_cubical(int n, const int64_t *dims, const void *vertex_weights,
+                                        wect_wtype wtype, int frac_bits, wect_stream stream,
+                                        wect_complex *out);
+
+/*
+ * Geometric simplicial complex in R^n (Section 3 "inputs": per dimension a list of vertex
+ * index rows and a weight per simplex).
+ *   n                ambient dimension, 1..3
+ *   n_vertices       k_0 >= 1
+ *   coords (dev)     [k_0][n] float64 vertex positions l(v), finite
+ *   max_dim          highest simplex dimension present, 0..3
+ *   counts (host)    [max_dim+1], counts[0] = k_0, counts[i] = k_i >= 0
+ *   simplices (host) [max_dim+1] device pointers; simplices[i] (i >= 1) is int32 [k_i][i+1],
+ *                    each index in [0, k_0); simplices[0] is ignored.  Closure under faces
+ *                    is not checked: the transform sums over exactly the simplices given.
+ *   vertex_weights   (dev) [k_0] of type wtype
+ *   sw_mode          WECT_SW_MAX_OF_VERTICES or WECT_SW_EXPLICIT
+ *   simplex_weights  (host) [max_dim+1] device pointers to int64 [k_i] fixed-point weights
+ *                    (EXPLICIT only; entry 0 overrides the vertex weights), else NULL.
+ * Errors: INVALID_ARG for bad sizes, indices or non-finite data; OVERFLOW when a weight
+ * magnitude reaches 2^40.
+ */
+WECT_API wect_status wect_complex_create_simplicial(int n, int64_t n_vertices, const double *coords, int max_dim,
+                                           const int64_t *counts, const int32_t *const *simplices,
+                                           const void *vertex_weights, wect_wtype wtype, int frac_bits,
+                                           wect_simplex_weight_mode sw_mode,
+                                           const int64_t *const *simplex_weights, wect_stream stream,
+                                           wect_complex *out);
+
+/*
+ * Replace the vertex weights of an existing complex (same count, same wtype, same frac_bits
+ * as at create time); asynchronous, allocates nothing.  For a simplicial complex in
+ * MAX_OF_VERTICES mode the simplex weights are recomputed on the device.  Weights larger than
+ * the accumulator chosen at create time set WECT_ERR_OVERFLOW in the device status word.
+ */
+WECT_API wect_status wect_complex_set_weights(wect_complex cx, const void *vertex_weights, wect_stream stream);
+
+/* Number of vertices k_0 (0 for a NULL handle). */
+WECT_API int64_t wect_complex_num_vertices(wect_complex cx);
+
+/* Number of cells of each dimension (host array of 4, zero beyond the top dimension). */
+WECT_API wect_status wect_complex_cell_counts(wect_complex cx, int64_t *counts4);
+
+/* Synchronise the stream, return and clear the device status word of the complex. */
+WECT_API wect_status wect_complex_device_status(wect_complex cx, wect_stream stream);
+
+WECT_API void wect_complex_destroy(wect_complex cx);
+
+/* ---------------------------------------------------------------- forward transform */
+
+/*
+ * WECT of cx over d directions (Definition "wect", Example "ex:wect", Algorithm 1).
+ *   dirs (dev)  [d][n] float64 direction vectors (finite; not required to be unit length)
+ *   d >= 1, T >= 2
+ *   lo, hi      threshold range; both NaN selects the paper's default [-M, M] with
+ *               M = max over directions and vertices of |h_p(v)| (computed exactly on the
+ *               device); otherwise lo <= hi, finite.
+ *   out (dev)   [d][T] int64, row p = WECF of direction p at thresholds beta[0..T-1]
+ */
+WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
+                         int64_t *out, wect_stream stream);
+
+/*
+ * ECF / WECF of cx for one vertex filter f (Eq. "ecf"; Remark "which-ecf": the ECF of an
+ * image when f is the pixel intensity and weighted = 0).
+ *   filter (dev) [k_0] float64, finite
+ *   weighted     0 => every cell has weight 1; otherwise the complex's weights
+ *   out (dev)    [T] int64
+ */
+WECT_API wect_status ecf_compute(wect_complex cx, const double *filter, int T, double lo, double hi, int weighted,
+                        int64_t *out, wect_stream stream);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/*
+ * Adjoint of wect_compute with respect to the vertex weights (the paper names differentiable
+ * transforms as future work, Section 6; this is the exact chain rule of Algorithm 1):
+ *   S[p][q]  = sum_{q' >= q} dW[p][q']                       (suffix sum of the upstream)
+ *   g(s)     = sum_p S[p][bin_p(s)]                           (per cell)
+ *   I_v      = sum over cells s whose heaviest vertex is v of (-1)^dim(s) g(s)
+ *              (ties of the heaviest vertex go to the lowest vertex index)
+ *   grad_w[v] = (float)((double)I_v * scale)
+ * I_v is accumulated exactly (128-bit); the per-direction sums S and g(s) are int64, so the
+ * upstream must satisfy d * max_q |S[p][q]| < 2^63 (else WECT_ERR_OVERFLOW is set in the device
+ * status word and grad_w is unspecified).  Only complexes whose cell weights are the max of
+ * their vertex weights (cubical, or simplicial in MAX_OF_VERTICES mode) are supported.
+ *   dW (dev)      [d][T] int64 upstream gradient in fixed-point units
+ *   grad_w (dev)  [k_0] float32
+ */
+WECT_API wect_status wect_backward(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
+                          const int64_t *dW, double scale, float *grad_w, wect_stream stream);
+
+/* ---------------------------------------------------------------- batches */
+
+/*
+ * A batch of cubical complexes computed by one persistent launch over a work queue of
+ * (complex, direction tile, row range) items ordered largest first.  The batch refers to the
+ * complexes' device data: they must outlive it.  All complexes must be cubical with the same n.
+ */
+WECT_API wect_status wect_batch_create(int count, const wect_complex *cxs, wect_batch *out);
+
+/*
+ * A batch that owns its complexes: count cubical grids of dimension n with per-complex axis
+ * lengths dims (host [count][n]) and one concatenated weight array (dev, complexes in order).
+ */
+WECT_API wect_status wect_batch_create_cubical(int count, int n, const int64_t *dims, const void *vertex_weights,
+                                      wect_wtype wtype, int frac_bits, wect_stream stream, wect_batch *out);
+
+/* Replace all weights of a batch made by wect_batch_create_cubical (one device copy). */
+WECT_API wect_status wect_batch_set_weights(wect_batch b, const void *vertex_weights, wect_stream stream);
+
+WECT_API int wect_batch_count(wect_batch b);
+WECT_API int64_t wect_batch_total_vertices(wect_batch b);
+
+/*
+ * WECT of every complex of the batch; out (dev) [count][d][T] int64.  The launch sequence is
+ * captured into a CUDA graph on first use for a given (dirs, d, T, range, out, stream) and
+ * replayed afterwards.  Tile shapes come from the batch's autotuner (wect_batch_autotune) or a
+ * size-based default.
+ */
+WECT_API wect_status wect_batch_compute(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                               int64_t *out, wect_stream stream);
+
+/* Same result as wect_batch_compute, launched as one ordinary kernel sequence per complex
+ * (the per-complex loop the batched path is measured against). */
+WECT_API wect_status wect_batch_compute_loop(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                    int64_t *out, wect_stream stream);
+
+/* Adjoint for every complex of the batch: dW (dev) [count][d][T], grad_w (dev) concatenated
+ * [sum of k_0] float32 in complex order. */
+WECT_API wect_status wect_batch_backward(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                const int64_t *dW, double scale, float *grad_w, wect_stream stream);
+
+/* Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest. */
+WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                int64_t *scratch_out, wect_stream stream);
+
+WECT_API void wect_batch_destroy(wect_batch b);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Thread-local message for the last non-OK status on this thread ("" if none). */
+WECT_API const char *wect_last_error(void);
+
+/* Library version string. */
+WECT_API const char *wect_version(void);
+
+/*
+ * Number of kernels this library launched (or replayed inside its graphs) on the calling
+ * process since load, for launch accounting.
+ */
+WECT_API int64_t wect_kernel_launch_count(void);
+
+/*
+ * Kernel timing hook for benchmarks.  While enabled, every compute call records a pair of CUDA
+ * events on its stream around its dominant kernel (the stencil or gather scatter kernel, or
+ * the replayed batch graph, or the adjoint's kernels).  wect_profile_read synchronises on the
+ * recorded events, returns the summed kernel milliseconds and the number of timed launches
+ * since the last read, and releases the events.
+ */
+WECT_API wect_status wect_profile_enable(int on);
+WECT_API wect_status wect_profile_read(double *kernel_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WECT_H */

@@ -1,0 +1,1377 @@
+// wect_api.cu -- the C ABI declared in include/wect.h: handles, validation, workspace,
+// dispatch to the kernels, batches (persistent launch + CUDA graph) and the tile autotuner.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/wect.h"
+#include "wect_device.cuh"
+#include "wect_launch.h"
+
+using namespace wect;
+
+// ------------------------------------------------------------------ errors and accounting
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+static wect_status fail(wect_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static wect_status cuda_fail(cudaError_t e, const char *where)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(WECT_ERR_OUT_OF_MEMORY, "%s: %s", where, cudaGetErrorString(e));
+    return fail(WECT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// a launch of one of our kernels (counted for launch accounting)
+#define KL(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+        g_launches.fetch_add(1, std::memory_order_relaxed); \
+    } while (0)
+
+// ------------------------------------------------------------------ profiling hook
+
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
+
+struct ProfScope {
+    cudaStream_t st;
+    cudaEvent_t e1 = nullptr;
+    explicit ProfScope(cudaStream_t s) : st(s)
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (!g_prof_on) return;
+        cudaEvent_t e0;
+        if (cudaEventCreate(&e0) != cudaSuccess) return;
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); e1 = nullptr; return; }
+        cudaEventRecord(e0, st);
+        g_prof_events.push_back({e0, e1});
+    }
+    ~ProfScope()
+    {
+        if (e1) cudaEventRecord(e1, st);
+    }
+};
+
+static bool range_is_default(double lo, double hi) { return std::isnan(lo) && std::isnan(hi); }
+
+static wect_status check_range(double lo, double hi, int T)
+{
+    if (T < 2) return fail(WECT_ERR_INVALID_ARG, "T must be >= 2 (got %d)", T);
+    if (T > 65535) return fail(WECT_ERR_UNSUPPORTED, "T must be <= 65535 (got %d)", T);
+    if (range_is_default(lo, hi)) return WECT_OK;
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return fail(WECT_ERR_INVALID_ARG, "lo/hi must be finite or both NaN");
+    if (lo > hi) return fail(WECT_ERR_INVALID_ARG, "lo > hi");
+    return WECT_OK;
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static size_t smem_optin()
+{
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (v <= 0) v = 48 * 1024;
+    }
+    return (size_t)v;
+}
+
+static size_t smem_per_sm()
+{
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (v <= 0) v = 100 * 1024;
+    }
+    return (size_t)v;
+}
+
+// ------------------------------------------------------------------ device buffers
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t cap = 0;   // elements
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= cap && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc((void **)&p, std::max<size_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) cap = std::max<size_t>(n, 1);
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Per-call workspace shared by the compute entry points of one complex or batch.
+struct Workspace {
+    DBuf<double> range;           // [6]: lo, hi, step, max|x_0..2|
+    DBuf<double> beta;            // [T]
+    DBuf<unsigned long long> M;   // [2]: max-abs bits, float lower-bound scratch
+    DBuf<int> counter;            // work-queue head
+    DBuf<int> perm, octb;         // octant grouping of the directions
+    DBuf<uint16_t> bins;          // vertex bins
+    DBuf<int64_t> S;              // suffix sums of the upstream gradient
+    DBuf<int64_t> Rv;             // per-vertex octant sums (adjoint)
+    DBuf<unsigned long long> Iacc;
+    DBuf<WorkItem> items;
+    DBuf<WorkItem> items_bwd;
+    // cache key of the uploaded item list
+    std::tuple<int, int, int, int, int> items_key{-1, -1, -1, -1, -1};
+    std::tuple<int, int> items_bwd_key{-1, -1};
+    int n_items = 0, n_items_bwd = 0;
+    void release()
+    {
+        range.release(); beta.release(); M.release(); counter.release(); perm.release(); octb.release();
+        bins.release(); S.release(); Rv.release(); Iacc.release(); items.release(); items_bwd.release();
+    }
+};
+
+// ------------------------------------------------------------------ handles
+
+struct wect_complex_s {
+    int kind = 0;                  // 0 = cubical, 1 = simplicial
+    int n = 0;
+    int64_t nv = 0;
+    int L[3] = {1, 1, 1};
+    int wtype = WECT_W_ONE;
+    int frac_bits = 0;
+    size_t wbytes = 0;             // bytes per raw vertex weight
+    void *d_w = nullptr;           // raw weights (cubical), owned unless borrowed
+    bool owns_w = true;
+    int nsplit = 1;
+    int64_t climit = 0;            // cubical: max |c_o(v)|; simplicial: max |w(s)|
+    int kflush = 1 << 16;
+    int64_t cells[4] = {0, 0, 0, 0};
+    // simplicial
+    double *d_coords = nullptr;
+    int max_dim = 0;
+    int64_t counts[4] = {0, 0, 0, 0};
+    int32_t *d_simp[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t *d_sw[4] = {nullptr, nullptr, nullptr, nullptr};   // d_sw[0] = vertex weights (fixed)
+    int sw_mode = WECT_SW_MAX_OF_VERTICES;
+    // device state
+    int *d_status = nullptr;
+    GridDesc *d_grid = nullptr;
+    Workspace ws;
+    std::mutex mu;
+};
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int nodes = 0;
+};
+
+struct BatchConfig {
+    int dpl = 0, Dt = 0, R = 0;
+};
+
+struct wect_batch_s {
+    int count = 0;
+    int n = 0;
+    int wtype = WECT_W_ONE;
+    int frac_bits = 0;
+    int nsplit = 1;
+    int64_t climit = 0;
+    int kflush = 1 << 16;
+    int64_t total_nv = 0;
+    int maxL0 = 1;
+    std::vector<GridDesc> h_grids;
+    std::vector<int64_t> v_off;
+    GridDesc *d_grids = nullptr;
+    int *d_status = nullptr;
+    void *d_w = nullptr;           // owned concatenated weights (create_cubical), else nullptr
+    size_t w_total_bytes = 0;
+    Workspace ws;
+    std::map<std::pair<int, int>, BatchConfig> tuned;    // (d, T) -> tile shape
+    std::vector<int> loop_starts;                        // per-complex item ranges of the loop path
+    std::map<std::tuple<const void *, int, int, double, double, void *, void *, int, int>, GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+    std::mutex mu;
+};
+
+static size_t wtype_bytes(int wt)
+{
+    switch (wt) {
+    case WECT_W_U8: return 1;
+    case WECT_W_I64_FIXED: return 8;
+    case WECT_W_F32: return 4;
+    default: return 0;
+    }
+}
+
+static wect_status check_wtype(int wt, int frac_bits)
+{
+    if (wt < WECT_W_U8 || wt > WECT_W_ONE) return fail(WECT_ERR_INVALID_ARG, "unknown weight type %d", wt);
+    if (wt == WECT_W_F32 && (frac_bits < 0 || frac_bits > 40))
+        return fail(WECT_ERR_INVALID_ARG, "frac_bits must be in [0, 40] (got %d)", frac_bits);
+    return WECT_OK;
+}
+
+// Accumulator mode of a cubical complex from the largest fixed-point vertex weight.  The
+// per-vertex contribution c_o(v) is a signed sum of 2^n cell weights, |c| <= 2^n max|w|.
+static wect_status choose_cubical_mode(int n, int wt, uint64_t wmax, int &nsplit, int64_t &climit, int &kflush)
+{
+    const int64_t two_n = 1ll << n;
+    if (wt == WECT_W_U8 || wt == WECT_W_ONE) {
+        climit = two_n * 255;
+        nsplit = 1;
+        kflush = (int)std::min<int64_t>((((int64_t)1 << 31) - 1) / climit, 1 << 30);
+        return WECT_OK;
+    }
+    const double cmax = (double)two_n * (double)wmax;
+    if (cmax <= (double)(1 << 14)) {              // narrow: one plane, 2x headroom for later weights
+        nsplit = 1;
+        climit = 1 << 15;
+        kflush = 1 << 16;
+        return WECT_OK;
+    }
+    if (cmax < 2147483647.0) {                   // two planes: low 16 bits + signed high part
+        nsplit = 2;
+        climit = 2147483647ll;
+        kflush = 1 << 16;
+        return WECT_OK;
+    }
+    return fail(WECT_ERR_OVERFLOW, "cell contributions 2^n*max|w| = %.3g exceed 2^31", cmax);
+}
+
+// ------------------------------------------------------------------ tile shapes (cubical)
+
+struct CubShape {
+    int dpl, Dt, R, ctas_per_sm, grid;
+    size_t smem;
+};
+
+// Directions per lane: 4 when the direction set fills a warp four times over, else fewer.
+static int pick_dpl(int d)
+{
+    if (d >= 128) return 4;
+    if (d >= 64) return 2;
+    return 1;
+}
+
+static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, int Dt_req, int R_req, CubShape &out, int dpl_req = 0)
+{
+    const int threads = cubical_fwd_threads();
+    const int warps = threads / 32;
+    const int dpl = dpl_req > 0 ? dpl_req : pick_dpl(d);
+    const int per_warp = 32 * dpl;
+    const size_t limit = smem_optin() - 1024;
+    int Dt_max = per_warp;
+    while (Dt_max < d && Dt_max * 2 <= per_warp * warps) Dt_max *= 2;
+    for (int Dt = (Dt_req > 0 ? Dt_req : Dt_max); Dt >= per_warp; Dt /= 2) {
+        const int WC = Dt / per_warp;
+        if (WC > warps || warps % WC) continue;
+        const int RG = warps / WC;
+        std::vector<int> Rs;
+        if (R_req > 0) Rs.push_back(R_req);
+        else for (int r = 4 * RG; r >= RG; r /= 2) Rs.push_back(r);
+        for (int R : Rs) {
+            if (R % RG) continue;
+            const size_t sm = cubical_fwd_smem(n, nsplit, T, Dt, R, maxL0);
+            if (sm > limit) continue;
+            out.dpl = dpl;
+            out.Dt = Dt;
+            out.R = R;
+            out.smem = sm;
+            const size_t per_sm = smem_per_sm();
+            int k = (int)(per_sm / (sm + 2048));
+            k = std::max(1, std::min(k, 2048 / threads));
+            out.ctas_per_sm = k;
+            out.grid = sm_count() * k;
+            return true;
+        }
+        if (Dt_req > 0) break;
+    }
+    return false;
+}
+
+// Items for a set of grids: per complex, direction tiles x row chunks, largest first.
+static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int R, int target_items,
+                                        bool whole)
+{
+    const int ntiles = (d + Dt - 1) / Dt;
+    std::vector<std::pair<int64_t, WorkItem>> v;
+    int64_t total_rows = 0;
+    for (auto &g : grids) total_rows += g.rows;
+    for (int c = 0; c < (int)grids.size(); ++c) {
+        const GridDesc &g = grids[c];
+        int chunks = 1;
+        if (!whole) {
+            const double share = (double)g.rows / (double)std::max<int64_t>(total_rows, 1);
+            chunks = (int)std::ceil(share * target_items / ntiles);
+            chunks = std::max(1, std::min(chunks, (g.rows + R - 1) / R));
+        }
+        int per = (g.rows + chunks - 1) / chunks;
+        per = ((per + R - 1) / R) * R;
+        for (int t = 0; t < ntiles; ++t)
+            for (int r0 = 0; r0 < g.rows; r0 += per) {
+                WorkItem w{c, t, r0, std::min(g.rows, r0 + per)};
+                v.push_back({(int64_t)(w.r1 - w.r0) * g.L[0], w});
+            }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<WorkItem> out;
+    out.reserve(v.size());
+    for (auto &x : v) out.push_back(x.second);
+    return out;
+}
+
+// ------------------------------------------------------------------ cubical launch sequence
+
+struct CubLaunch {
+    int n, nsplit, wt, frac_bits, kflush, maxL0;
+    int64_t climit;
+    const GridDesc *d_grids;
+    Workspace *ws;
+};
+
+// Enqueue the forward transform of a set of grids: [range], beta, work queue, stencil kernel,
+// [scan].  items must be uploaded in ws->items already.
+static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, int n_items, bool direct,
+                                       const double *dirs, int d, int T, double lo, double hi, bool dflt,
+                                       int64_t out_rows, int64_t *out, cudaStream_t st)
+{
+    Workspace &ws = *L.ws;
+    if (dflt) {
+        CK(cudaMemsetAsync(ws.M.p, 0, sizeof(unsigned long long), st), "memset");
+        KL(launch_grid_max_abs(L.n, L.d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
+    }
+    KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, ws.M.p, T, ws.range.p, ws.beta.p, st), "setup_range_beta");
+    CK(cudaMemsetAsync(ws.counter.p, 0, sizeof(int), st), "memset");
+    if (!direct) CK(cudaMemsetAsync(out, 0, (size_t)out_rows * T * sizeof(int64_t), st), "memset");
+    CubicalFwdArgs a{};
+    a.grids = L.d_grids;
+    a.items = ws.items.p;
+    a.n_items = n_items;
+    a.counter = ws.counter.p;
+    a.dirs = dirs;
+    a.d = d;
+    a.T = T;
+    a.range = ws.range.p;
+    a.beta = ws.beta.p;
+    a.Dt = sh.Dt;
+    a.R = sh.R;
+    a.CP = cubical_fwd_pitch(L.n, sh.R, L.maxL0);
+    a.wt = L.wt;
+    a.kflush = L.kflush;
+    a.frac_bits = L.frac_bits;
+    a.climit = L.climit;
+    a.direct = direct ? 1 : 0;
+    a.out = reinterpret_cast<unsigned long long *>(out);
+    const int grid = std::max(1, std::min(sh.grid, n_items));
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusNone) {
+            ProfScope prof(st);
+            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, a, grid, sh.smem, st), "cubical_fwd");
+        } else {
+            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, a, grid, sh.smem, st), "cubical_fwd");
+        }
+    }
+    if (!direct) KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), out_rows, T, st), "scan_rows");
+    return WECT_OK;
+}
+
+static wect_status ensure_common_ws(Workspace &ws, int T)
+{
+    CK(ws.range.ensure(6), "alloc");
+    CK(ws.beta.ensure((size_t)T), "alloc");
+    CK(ws.M.ensure(2), "alloc");
+    CK(ws.counter.ensure(1), "alloc");
+    return WECT_OK;
+}
+
+static wect_status upload_items(Workspace &ws, const std::vector<WorkItem> &items, cudaStream_t st)
+{
+    CK(ws.items.ensure(items.size()), "alloc");
+    CK(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
+       "upload items");
+    CK(cudaStreamSynchronize(st), "sync");     // the host vector goes out of scope
+    ws.n_items = (int)items.size();
+    return WECT_OK;
+}
+
+// ------------------------------------------------------------------ create / destroy
+
+static wect_status new_status_word(int **p)
+{
+    CK(cudaMalloc((void **)p, sizeof(int)), "alloc");
+    CK(cudaMemset(*p, 0, sizeof(int)), "memset");
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, const void *vertex_weights,
+                                                   wect_wtype wtype, int frac_bits, wect_stream stream,
+                                                   wect_complex *out)
+{
+    if (!out) return fail(WECT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 3) return fail(WECT_ERR_INVALID_ARG, "n must be 1..3 (got %d)", n);
+    if (!dims) return fail(WECT_ERR_INVALID_ARG, "dims is NULL");
+    wect_status s = check_wtype(wtype, frac_bits);
+    if (s) return s;
+    int64_t nv = 1;
+    for (int a = 0; a < n; ++a) {
+        if (dims[a] < 1 || dims[a] > (1 << 24)) return fail(WECT_ERR_INVALID_ARG, "dims[%d] = %lld out of range", a, (long long)dims[a]);
+        nv *= dims[a];
+        if (nv >= (1ll << 31)) return fail(WECT_ERR_INVALID_ARG, "grid has >= 2^31 vertices");
+    }
+    if (wtype != WECT_W_ONE && !vertex_weights) return fail(WECT_ERR_INVALID_ARG, "vertex_weights is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *c = new wect_complex_s();
+    c->kind = 0;
+    c->n = n;
+    c->nv = nv;
+    for (int a = 0; a < n; ++a) c->L[a] = (int)dims[a];
+    c->wtype = wtype;
+    c->frac_bits = (wtype == WECT_W_F32) ? frac_bits : 0;
+    c->wbytes = wtype_bytes(wtype);
+    // cells per dimension: number of (corner, mask) boxes with |mask| = k
+    for (int e = 0; e < (1 << n); ++e) {
+        int64_t cnt = 1;
+        for (int a = 0; a < n; ++a) cnt *= ((e >> a) & 1) ? (c->L[a] - 1) : c->L[a];
+        c->cells[__builtin_popcount(e)] += cnt;
+    }
+    auto cleanup = [&](wect_status st_) { wect_complex_destroy(c); return st_; };
+    if ((s = new_status_word(&c->d_status))) return cleanup(s);
+    if (c->wbytes) {
+        cudaError_t e = cudaMalloc(&c->d_w, (size_t)nv * c->wbytes);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "alloc weights"));
+        e = cudaMemcpyAsync(c->d_w, vertex_weights, (size_t)nv * c->wbytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "copy weights"));
+    }
+    if ((s = ensure_common_ws(c->ws, 2))) return cleanup(s);
+    int *d_bad = c->d_status;   // reuse the status word as a flag before it is published
+    uint64_t wmax = 255;
+    if (wtype == WECT_W_F32 || wtype == WECT_W_I64_FIXED) {
+        cudaError_t e = cudaMemsetAsync(c->ws.M.p, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, c->d_w, nv, c->frac_bits, nullptr, c->ws.M.p, d_bad, st);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "weights_to_fixed"));
+        g_launches++;
+        unsigned long long m = 0;
+        int bad = 0;
+        e = cudaMemcpyAsync(&m, c->ws.M.p, sizeof m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "create sync"));
+        if (bad) return cleanup(fail(WECT_ERR_INVALID_ARG, "vertex weights are not finite or too large for int64 fixed point"));
+        wmax = m;
+    } else {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "create sync"));
+    }
+    if ((s = choose_cubical_mode(n, wtype, wmax, c->nsplit, c->climit, c->kflush))) return cleanup(s);
+    GridDesc g{};
+    g.w = c->d_w;
+    for (int a = 0; a < 3; ++a) g.L[a] = c->L[a];
+    g.rows = c->L[1] * c->L[2];
+    g.nv = nv;
+    g.v_off = 0;
+    g.status = c->d_status;
+    cudaError_t e = cudaMalloc((void **)&c->d_grid, sizeof(GridDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload grid"));
+    *out = c;
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices, const double *coords, int max_dim,
+                                                      const int64_t *counts, const int32_t *const *simplices,
+                                                      const void *vertex_weights, wect_wtype wtype, int frac_bits,
+                                                      wect_simplex_weight_mode sw_mode,
+                                                      const int64_t *const *simplex_weights, wect_stream stream,
+                                                      wect_complex *out)
+{
+    if (!out) return fail(WECT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 3) return fail(WECT_ERR_INVALID_ARG, "n must be 1..3 (got %d)", n);
+    if (n_vertices < 1 || n_vertices >= (1ll << 31)) return fail(WECT_ERR_INVALID_ARG, "n_vertices out of range");
+    if (max_dim < 0 || max_dim > 3) return fail(WECT_ERR_INVALID_ARG, "max_dim must be 0..3");
+    if (!coords || !counts) return fail(WECT_ERR_INVALID_ARG, "coords/counts is NULL");
+    if (counts[0] != n_vertices) return fail(WECT_ERR_INVALID_ARG, "counts[0] must equal n_vertices");
+    if (sw_mode != WECT_SW_MAX_OF_VERTICES && sw_mode != WECT_SW_EXPLICIT)
+        return fail(WECT_ERR_INVALID_ARG, "unknown simplex weight mode");
+    wect_status s = check_wtype(wtype, frac_bits);
+    if (s) return s;
+    for (int i = 1; i <= max_dim; ++i) {
+        if (counts[i] < 0 || counts[i] >= (1ll << 31)) return fail(WECT_ERR_INVALID_ARG, "counts[%d] out of range", i);
+        if (counts[i] > 0 && (!simplices || !simplices[i])) return fail(WECT_ERR_INVALID_ARG, "simplices[%d] is NULL", i);
+        if (sw_mode == WECT_SW_EXPLICIT && counts[i] > 0 && (!simplex_weights || !simplex_weights[i]))
+            return fail(WECT_ERR_INVALID_ARG, "simplex_weights[%d] is NULL", i);
+    }
+    const bool vw_explicit = sw_mode == WECT_SW_EXPLICIT && simplex_weights && simplex_weights[0];
+    if (!vw_explicit && wtype != WECT_W_ONE && !vertex_weights) return fail(WECT_ERR_INVALID_ARG, "vertex_weights is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *c = new wect_complex_s();
+    c->kind = 1;
+    c->n = n;
+    c->nv = n_vertices;
+    c->max_dim = max_dim;
+    c->wtype = wtype;
+    c->frac_bits = (wtype == WECT_W_F32) ? frac_bits : 0;
+    c->wbytes = wtype_bytes(wtype);
+    c->sw_mode = sw_mode;
+    for (int i = 0; i <= max_dim; ++i) c->counts[i] = counts[i];
+    for (int i = 0; i <= max_dim; ++i) c->cells[i] = counts[i];
+    auto cleanup = [&](wect_status st_) { wect_complex_destroy(c); return st_; };
+    cudaError_t e;
+    if ((s = new_status_word(&c->d_status))) return cleanup(s);
+    if ((s = ensure_common_ws(c->ws, 2))) return cleanup(s);
+    int *d_bad = nullptr;
+    if ((e = cudaMalloc((void **)&d_bad, 4 * sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "alloc"));
+    struct FreeBad { int *p; ~FreeBad() { if (p) cudaFree(p); } } fb{d_bad};
+    if ((e = cudaMemsetAsync(d_bad, 0, 4 * sizeof(int), st)) != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
+    // coordinates
+    if ((e = cudaMalloc((void **)&c->d_coords, (size_t)n_vertices * n * sizeof(double))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "alloc coords"));
+    if ((e = cudaMemcpyAsync(c->d_coords, coords, (size_t)n_vertices * n * sizeof(double), cudaMemcpyDeviceToDevice, st)))
+        return cleanup(cuda_fail(e, "copy coords"));
+    if ((e = launch_finite_check(c->d_coords, n_vertices * n, d_bad + 0, 1, st))) return cleanup(cuda_fail(e, "finite_check"));
+    g_launches++;
+    // per-axis max |x| into range[3..5]
+    std::vector<unsigned long long> zeros(3, 0ull);
+    unsigned long long *d_xm = reinterpret_cast<unsigned long long *>(c->ws.range.p + 3);
+    if ((e = cudaMemsetAsync(c->ws.range.p, 0, 6 * sizeof(double), st))) return cleanup(cuda_fail(e, "memset"));
+    for (int a = 0; a < n; ++a) {
+        if ((e = launch_max_abs_f64(c->d_coords, n_vertices, n, a, d_xm + a, st))) return cleanup(cuda_fail(e, "max_abs"));
+        g_launches++;
+    }
+    // simplex lists
+    for (int i = 1; i <= max_dim; ++i) {
+        const size_t cnt = (size_t)counts[i] * (i + 1);
+        if ((e = cudaMalloc((void **)&c->d_simp[i], std::max<size_t>(cnt, 1) * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc"));
+        if (cnt) {
+            if ((e = cudaMemcpyAsync(c->d_simp[i], simplices[i], cnt * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)))
+                return cleanup(cuda_fail(e, "copy simplices"));
+            if ((e = launch_index_check(c->d_simp[i], (int64_t)cnt, n_vertices, d_bad + 1, st))) return cleanup(cuda_fail(e, "index_check"));
+            g_launches++;
+        }
+    }
+    // weights
+    for (int i = 0; i <= max_dim; ++i)
+        if ((e = cudaMalloc((void **)&c->d_sw[i], std::max<int64_t>(counts[i], 1) * sizeof(int64_t))))
+            return cleanup(cuda_fail(e, "alloc weights"));
+    if ((e = cudaMemsetAsync(c->ws.M.p, 0, 2 * sizeof(unsigned long long), st))) return cleanup(cuda_fail(e, "memset"));
+    if (vw_explicit) {
+        if ((e = cudaMemcpyAsync(c->d_sw[0], simplex_weights[0], n_vertices * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)))
+            return cleanup(cuda_fail(e, "copy"));
+        if ((e = launch_weights_to_fixed(WT_I64, c->d_sw[0], n_vertices, 0, nullptr, c->ws.M.p, d_bad + 2, st)))
+            return cleanup(cuda_fail(e, "weights"));
+        g_launches++;
+    } else {
+        if ((e = launch_weights_to_fixed(wtype, vertex_weights, n_vertices, c->frac_bits, c->d_sw[0], c->ws.M.p, d_bad + 2, st)))
+            return cleanup(cuda_fail(e, "weights"));
+        g_launches++;
+    }
+    for (int i = 1; i <= max_dim; ++i) {
+        if (counts[i] == 0) continue;
+        if (sw_mode == WECT_SW_EXPLICIT) {
+            if ((e = cudaMemcpyAsync(c->d_sw[i], simplex_weights[i], counts[i] * sizeof(int64_t), cudaMemcpyDeviceToDevice, st)))
+                return cleanup(cuda_fail(e, "copy"));
+            if ((e = launch_weights_to_fixed(WT_I64, c->d_sw[i], counts[i], 0, nullptr, c->ws.M.p, d_bad + 2, st)))
+                return cleanup(cuda_fail(e, "weights"));
+        } else {
+            if ((e = launch_simplex_weights_max(c->d_simp[i], counts[i], i + 1, c->d_sw[0], c->d_sw[i], st)))
+                return cleanup(cuda_fail(e, "simplex weights"));
+        }
+        g_launches++;
+    }
+    int bad[4] = {0, 0, 0, 0};
+    unsigned long long wmax = 0;
+    double xm[3] = {0, 0, 0};
+    if ((e = cudaMemcpyAsync(bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(&wmax, c->ws.M.p, sizeof wmax, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(xm, c->ws.range.p + 3, sizeof xm, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cleanup(cuda_fail(e, "create sync"));
+    if (bad[0]) return cleanup(fail(WECT_ERR_INVALID_ARG, "coordinates are not finite"));
+    if (bad[1]) return cleanup(fail(WECT_ERR_INVALID_ARG, "a simplex vertex index is outside [0, n_vertices)"));
+    if (bad[2]) return cleanup(fail(WECT_ERR_INVALID_ARG, "vertex weights are not finite or too large"));
+    if (wtype == WECT_W_U8 || wtype == WECT_W_ONE) wmax = std::max<unsigned long long>(wmax, 255);
+    if (wmax >= (1ull << 40)) return cleanup(fail(WECT_ERR_OVERFLOW, "a weight magnitude reaches 2^40"));
+    // accumulator: one int32 plane when 65536 updates of max|w| fit, else low 16 bits + high part
+    if (wmax <= (1ull << 14)) {
+        c->nsplit = 1;
+        c->climit = 1 << 15;
+        c->kflush = 1 << 16;
+    } else {
+        c->nsplit = 2;
+        const int64_t lim = (int64_t)std::max<unsigned long long>(wmax, 1ull << 31) * 2;    // headroom for later weights
+        c->climit = std::min<int64_t>(lim, (1ll << 40) - 1);
+        const int64_t hb = (c->climit >> 16) + 1;
+        c->kflush = (int)std::max<int64_t>(1, std::min<int64_t>(1 << 16, (((int64_t)1 << 31) - 1) / hb));
+    }
+    *out = c;
+    return WECT_OK;
+}
+
+extern "C" void wect_complex_destroy(wect_complex c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    if (c->owns_w && c->d_w) cudaFree(c->d_w);
+    if (c->d_coords) cudaFree(c->d_coords);
+    for (int i = 0; i < 4; ++i) {
+        if (c->d_simp[i]) cudaFree(c->d_simp[i]);
+        if (c->d_sw[i]) cudaFree(c->d_sw[i]);
+    }
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->d_grid) cudaFree(c->d_grid);
+    c->ws.release();
+    delete c;
+}
+
+extern "C" int64_t wect_complex_num_vertices(wect_complex c) { return c ? c->nv : 0; }
+
+extern "C" wect_status wect_complex_cell_counts(wect_complex c, int64_t *counts4)
+{
+    if (!c || !counts4) return fail(WECT_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i < 4; ++i) counts4[i] = c->cells[i];
+    return WECT_OK;
+}
+
+static wect_status status_from_bits(int bits)
+{
+    if (bits & kStatusOverflow) return fail(WECT_ERR_OVERFLOW, "weights exceeded the accumulator chosen at create time");
+    if (bits & kStatusTimeout) return fail(WECT_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (bits & kStatusBadIndex) return fail(WECT_ERR_INVALID_ARG, "device-side validation failed (non-finite input)");
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_complex_device_status(wect_complex c, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    cudaStream_t st = (cudaStream_t)stream;
+    int bits = 0;
+    CK(cudaStreamSynchronize(st), "sync");
+    CK(cudaMemcpy(&bits, c->d_status, sizeof bits, cudaMemcpyDeviceToHost), "read status");
+    CK(cudaMemset(c->d_status, 0, sizeof(int)), "clear status");
+    return status_from_bits(bits);
+}
+
+extern "C" wect_status wect_complex_set_weights(wect_complex c, const void *w, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->wtype == WECT_W_ONE) return WECT_OK;
+    if (!w) return fail(WECT_ERR_INVALID_ARG, "weights is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->kind == 0) {
+        CK(cudaMemcpyAsync(c->d_w, w, (size_t)c->nv * c->wbytes, cudaMemcpyDeviceToDevice, st), "copy weights");
+        KL(launch_weights_check(c->wtype, c->d_w, c->nv, c->frac_bits, c->climit >> c->n, c->d_status, st), "weights_check");
+        return WECT_OK;
+    }
+    if (c->sw_mode == WECT_SW_EXPLICIT) return fail(WECT_ERR_UNSUPPORTED, "set_weights on a complex with explicit simplex weights");
+    KL(launch_weights_to_fixed(c->wtype, w, c->nv, c->frac_bits, c->d_sw[0], nullptr, c->d_status, st), "weights_to_fixed");
+    KL(launch_weights_check(WT_I64, c->d_sw[0], c->nv, 0, c->climit, c->d_status, st), "weights_check");
+    for (int i = 1; i <= c->max_dim; ++i)
+        if (c->counts[i] > 0) KL(launch_simplex_weights_max(c->d_simp[i], c->counts[i], i + 1, c->d_sw[0], c->d_sw[i], st), "sw");
+    return WECT_OK;
+}
+
+// ------------------------------------------------------------------ forward
+
+static wect_status dirs_check(wect_complex c, const double *dirs, int d, cudaStream_t st)
+{
+    KL(launch_finite_check(dirs, (int64_t)d * c->n, c->d_status, kStatusBadIndex, st), "finite_check");
+    return WECT_OK;
+}
+
+static wect_status cubical_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi, int64_t *out,
+                                   cudaStream_t st)
+{
+    CubShape sh;
+    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], 0, 0, sh))
+        return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
+    wect_status s = ensure_common_ws(c->ws, T);
+    if (s) return s;
+    const int rows = c->L[1] * c->L[2];
+    const bool direct = false;
+    auto key = std::make_tuple(d, T, sh.Dt, sh.R, sh.grid);
+    if (c->ws.items_key != key) {
+        std::vector<GridDesc> gv(1);
+        gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
+        gv[0].rows = rows;
+        gv[0].nv = c->nv;
+        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, sh.R, sh.grid, false);
+        if ((s = upload_items(c->ws, items, st))) return s;
+        c->ws.items_key = key;
+    }
+    CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, c->L[0], c->climit, c->d_grid, &c->ws};
+    return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st);
+}
+
+static wect_status simplicial_range(wect_complex c, const double *dirs, int d, int T, double lo, double hi, cudaStream_t st)
+{
+    const bool dflt = range_is_default(lo, hi);
+    if (dflt) {
+        CK(cudaMemsetAsync(c->ws.M.p, 0, 2 * sizeof(unsigned long long), st), "memset");
+        KL(launch_simplicial_max_abs(c->n, c->d_coords, c->nv, dirs, d, c->ws.M.p,
+                                     reinterpret_cast<float *>(c->ws.M.p + 1), st), "max_abs");
+        g_launches++;    // two passes
+    }
+    KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
+    return WECT_OK;
+}
+
+static wect_status simplicial_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                      int64_t *out, cudaStream_t st)
+{
+    const int Dt = 32;
+    const size_t sm = simplex_fwd_smem(c->nsplit, T, Dt);
+    if (sm > std::min<size_t>(smem_optin(), 200 * 1024))
+        return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
+    wect_status s = ensure_common_ws(c->ws, T);
+    if (s) return s;
+    CK(c->ws.bins.ensure((size_t)c->nv * Dt), "alloc bins");
+    if ((s = simplicial_range(c, dirs, d, T, lo, hi, st))) return s;
+    CK(cudaMemsetAsync(out, 0, (size_t)d * T * sizeof(int64_t), st), "memset");
+    const int grid = sm_count();
+    ProfScope prof(st);
+    for (int dt = 0; dt * Dt < d; ++dt) {
+        KL(launch_vertex_bins(c->n, c->d_coords, c->nv, dirs, d, dt, Dt, T, c->ws.range.p, c->ws.beta.p, c->ws.bins.p, st),
+           "vertex_bins");
+        for (int i = 0; i <= c->max_dim; ++i) {
+            if (c->counts[i] == 0) continue;
+            SimplexFwdArgs a{};
+            a.simp = (i == 0) ? nullptr : c->d_simp[i];
+            a.sw = c->d_sw[i];
+            a.k = c->counts[i];
+            a.m = i + 1;
+            a.sign = (i & 1) ? -1 : 1;
+            a.bins = c->ws.bins.p;
+            a.Dt = Dt;
+            a.dtile = dt;
+            a.d = d;
+            a.T = T;
+            a.chunk = std::min<int64_t>(c->kflush, std::max<int64_t>(4096, (a.k + grid - 1) / grid));
+            a.out = reinterpret_cast<unsigned long long *>(out);
+            const int g = (int)std::min<int64_t>(grid, (a.k + a.chunk - 1) / a.chunk);
+            KL(launch_simplex_fwd(c->nsplit, a, std::max(g, 1), st), "simplex_fwd");
+        }
+    }
+    KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), d, T, st), "scan_rows");
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                    int64_t *out, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    if (!dirs || !out) return fail(WECT_ERR_INVALID_ARG, "dirs/out is NULL");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if ((s = dirs_check(c, dirs, d, st))) return s;
+    return c->kind == 0 ? cubical_compute(c, dirs, d, T, lo, hi, out, st) : simplicial_compute(c, dirs, d, T, lo, hi, out, st);
+}
+
+extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, double lo, double hi, int weighted,
+                                   int64_t *out, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    if (!filter || !out) return fail(WECT_ERR_INVALID_ARG, "filter/out is NULL");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if ((s = ensure_common_ws(c->ws, T))) return s;
+    CK(c->ws.bins.ensure((size_t)c->nv), "alloc bins");
+    KL(launch_finite_check(filter, c->nv, c->d_status, kStatusBadIndex, st), "finite_check");
+    const bool dflt = range_is_default(lo, hi);
+    if (dflt) {
+        CK(cudaMemsetAsync(c->ws.M.p, 0, sizeof(unsigned long long), st), "memset");
+        KL(launch_max_abs_f64(filter, c->nv, 1, 0, c->ws.M.p, st), "max_abs");
+    }
+    KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
+    KL(launch_filter_bins(filter, c->nv, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, st), "filter_bins");
+    CK(cudaMemsetAsync(out, 0, (size_t)T * sizeof(int64_t), st), "memset");
+    if (c->kind == 0) {
+        KL(launch_cubical_ecf(c->n, weighted ? c->wtype : WECT_W_ONE, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0,
+                              c->frac_bits, reinterpret_cast<unsigned long long *>(out), c->nv, st),
+           "cubical_ecf");
+    } else {
+        for (int i = 0; i <= c->max_dim; ++i) {
+            if (c->counts[i] == 0) continue;
+            KL(launch_simplex_ecf(i == 0 ? nullptr : c->d_simp[i], c->d_sw[i], c->counts[i], i + 1, (i & 1) ? -1 : 1,
+                                  weighted ? 1 : 0, c->ws.bins.p, T, reinterpret_cast<unsigned long long *>(out), st),
+               "simplex_ecf");
+        }
+    }
+    KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), 1, T, st), "scan_rows");
+    return WECT_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+
+static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const std::vector<GridDesc> &h_grids, int n,
+                                    int wt, int frac_bits, int64_t total_nv, Workspace &ws, const double *dirs, int d,
+                                    int T, double lo, double hi, const int64_t *dW, double scale, float *grad,
+                                    int *status, cudaStream_t st)
+{
+    if (range_is_default(lo, hi) && n_grids != 1) return fail(WECT_ERR_UNSUPPORTED, "default range in a batch");
+    wect_status s = ensure_common_ws(ws, T);
+    if (s) return s;
+    const int noct = 1 << n;
+    CK(ws.S.ensure((size_t)n_grids * d * T), "alloc S");
+    CK(ws.Rv.ensure((size_t)total_nv * noct), "alloc Rv");
+    CK(ws.perm.ensure((size_t)d), "alloc perm");
+    CK(ws.octb.ensure(9), "alloc octb");
+    const int R = 8;
+    const size_t sm = cubical_bwd_rsum_smem(d, R);
+    if (sm > std::min<size_t>(smem_optin(), 200 * 1024)) return fail(WECT_ERR_UNSUPPORTED, "d too large for the adjoint");
+    auto key = std::make_tuple(d, R);
+    if (ws.items_bwd_key != key) {
+        std::vector<WorkItem> items;
+        for (int c = 0; c < n_grids; ++c) {
+            const int rows = h_grids[c].rows;
+            const int per = std::max(R, ((std::max(1, 4096 / std::max(1, h_grids[c].L[0])) + R - 1) / R) * R);
+            for (int r0 = 0; r0 < rows; r0 += per) items.push_back(WorkItem{c, 0, r0, std::min(rows, r0 + per)});
+        }
+        CK(ws.items_bwd.ensure(items.size()), "alloc");
+        CK(cudaMemcpyAsync(ws.items_bwd.p, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st), "upload");
+        CK(cudaStreamSynchronize(st), "sync");
+        ws.n_items_bwd = (int)items.size();
+        ws.items_bwd_key = key;
+    }
+    const bool dflt = range_is_default(lo, hi);
+    if (dflt) {
+        CK(cudaMemsetAsync(ws.M.p, 0, sizeof(unsigned long long), st), "memset");
+        KL(launch_grid_max_abs(n, d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
+    }
+    KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, ws.M.p, T, ws.range.p, ws.beta.p, st), "setup_range_beta");
+    KL(launch_suffix_rows(dW, ws.S.p, (int64_t)n_grids * d, T, INT64_MAX / d, status, st), "suffix_rows");
+    KL(launch_octant_sort(n, dirs, d, ws.perm.p, ws.octb.p, st), "octant_sort");
+    CubicalBwdArgs a{};
+    a.grids = d_grids;
+    a.n_grids = n_grids;
+    a.items = ws.items_bwd.p;
+    a.dirs = dirs;
+    a.d = d;
+    a.T = T;
+    a.range = ws.range.p;
+    a.beta = ws.beta.p;
+    a.perm = ws.perm.p;
+    a.octb = ws.octb.p;
+    a.R = R;
+    a.S = ws.S.p;
+    a.Rv = ws.Rv.p;
+    a.grad = grad;
+    a.scale = scale;
+    a.frac_bits = frac_bits;
+    a.total_nv = total_nv;
+    {
+        ProfScope prof(st);
+        KL(launch_cubical_bwd(n, wt, a, ws.n_items_bwd, sm, st), "cubical_bwd");
+    }
+    g_launches++;   // rsum + route
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                     const int64_t *dW, double scale, float *grad_w, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    if (!dirs || !dW || !grad_w) return fail(WECT_ERR_INVALID_ARG, "NULL pointer argument");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    if (!std::isfinite(scale)) return fail(WECT_ERR_INVALID_ARG, "scale must be finite");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if ((s = dirs_check(c, dirs, d, st))) return s;
+    if (c->kind == 0) {
+        std::vector<GridDesc> hg(1);
+        hg[0].L[0] = c->L[0]; hg[0].L[1] = c->L[1]; hg[0].L[2] = c->L[2];
+        hg[0].rows = c->L[1] * c->L[2];
+        hg[0].nv = c->nv;
+        return cubical_backward(c->d_grid, 1, hg, c->n, c->wtype, c->frac_bits, c->nv, c->ws, dirs, d, T, lo, hi, dW, scale,
+                                grad_w, c->d_status, st);
+    }
+    if (c->sw_mode != WECT_SW_MAX_OF_VERTICES)
+        return fail(WECT_ERR_UNSUPPORTED, "the adjoint needs simplex weights that are the max of the vertex weights");
+    if ((s = ensure_common_ws(c->ws, T))) return s;
+    CK(c->ws.S.ensure((size_t)d * T), "alloc S");
+    CK(c->ws.bins.ensure((size_t)c->nv * 32), "alloc bins");
+    CK(c->ws.Iacc.ensure((size_t)c->nv * 2), "alloc Iacc");
+    if ((s = simplicial_range(c, dirs, d, T, lo, hi, st))) return s;
+    KL(launch_suffix_rows(dW, c->ws.S.p, d, T, INT64_MAX / d, c->d_status, st), "suffix_rows");
+    const int32_t *simp[4] = {nullptr, c->d_simp[1], c->d_simp[2], c->d_simp[3]};
+    CK(launch_simplicial_bwd(c->n, c->d_coords, c->nv, simp, c->counts, c->max_dim, c->d_sw[0], dirs, d, T, c->ws.range.p,
+                             c->ws.beta.p, c->ws.S.p, c->ws.bins.p, c->ws.Iacc.p, grad_w, scale, st),
+       "simplicial_bwd");
+    g_launches += 1 + ((d + 31) / 32) * (1 + c->max_dim + 1);
+    return WECT_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+static wect_status batch_finish(wect_batch b, cudaStream_t st)
+{
+    b->v_off.resize(b->count);
+    int64_t off = 0;
+    b->maxL0 = 1;
+    for (int i = 0; i < b->count; ++i) {
+        b->h_grids[i].v_off = off;
+        b->v_off[i] = off;
+        off += b->h_grids[i].nv;
+        b->maxL0 = std::max(b->maxL0, b->h_grids[i].L[0]);
+    }
+    b->total_nv = off;
+    CK(cudaMalloc((void **)&b->d_grids, b->h_grids.size() * sizeof(GridDesc)), "alloc grids");
+    CK(cudaMemcpy(b->d_grids, b->h_grids.data(), b->h_grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice), "upload grids");
+    CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+    (void)st;
+    return ensure_common_ws(b->ws, 2);
+}
+
+extern "C" wect_status wect_batch_create(int count, const wect_complex *cxs, wect_batch *out)
+{
+    if (!out) return fail(WECT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !cxs) return fail(WECT_ERR_INVALID_ARG, "empty batch");
+    const wect_complex c0 = cxs[0];
+    if (!c0) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    for (int i = 0; i < count; ++i) {
+        const wect_complex c = cxs[i];
+        if (!c || c->kind != 0) return fail(WECT_ERR_UNSUPPORTED, "batches hold cubical complexes only");
+        if (c->n != c0->n || c->wtype != c0->wtype || c->frac_bits != c0->frac_bits)
+            return fail(WECT_ERR_INVALID_ARG, "batch complexes must share n, weight type and frac_bits");
+    }
+    auto *b = new wect_batch_s();
+    b->count = count;
+    b->n = c0->n;
+    b->wtype = c0->wtype;
+    b->frac_bits = c0->frac_bits;
+    b->nsplit = 1;
+    b->climit = INT64_MAX;
+    b->kflush = 1 << 30;
+    for (int i = 0; i < count; ++i) {
+        b->nsplit = std::max(b->nsplit, cxs[i]->nsplit);
+        b->kflush = std::min(b->kflush, cxs[i]->kflush);
+    }
+    for (int i = 0; i < count; ++i)
+        if (cxs[i]->nsplit == b->nsplit) b->climit = std::min(b->climit, cxs[i]->climit);
+    b->h_grids.resize(count);
+    for (int i = 0; i < count; ++i) {
+        GridDesc g{};
+        g.w = cxs[i]->d_w;
+        for (int a = 0; a < 3; ++a) g.L[a] = cxs[i]->L[a];
+        g.rows = g.L[1] * g.L[2];
+        g.nv = cxs[i]->nv;
+        g.status = cxs[i]->d_status;
+        b->h_grids[i] = g;
+    }
+    cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc"); }
+    wect_status s = batch_finish(b, nullptr);
+    if (s) { wect_batch_destroy(b); return s; }
+    *out = b;
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t *dims, const void *vertex_weights,
+                                                 wect_wtype wtype, int frac_bits, wect_stream stream, wect_batch *out)
+{
+    if (!out) return fail(WECT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !dims) return fail(WECT_ERR_INVALID_ARG, "empty batch");
+    if (n < 1 || n > 3) return fail(WECT_ERR_INVALID_ARG, "n must be 1..3");
+    wect_status s = check_wtype(wtype, frac_bits);
+    if (s) return s;
+    if (wtype != WECT_W_ONE && !vertex_weights) return fail(WECT_ERR_INVALID_ARG, "vertex_weights is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto *b = new wect_batch_s();
+    b->count = count;
+    b->n = n;
+    b->wtype = wtype;
+    b->frac_bits = (wtype == WECT_W_F32) ? frac_bits : 0;
+    b->h_grids.resize(count);
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        int64_t nv = 1;
+        GridDesc g{};
+        g.L[0] = g.L[1] = g.L[2] = 1;
+        for (int a = 0; a < n; ++a) {
+            const int64_t L = dims[(int64_t)i * n + a];
+            if (L < 1 || L > (1 << 24)) { delete b; return fail(WECT_ERR_INVALID_ARG, "dims out of range"); }
+            g.L[a] = (int)L;
+            nv *= L;
+        }
+        if (nv >= (1ll << 31)) { delete b; return fail(WECT_ERR_INVALID_ARG, "grid too large"); }
+        g.rows = g.L[1] * g.L[2];
+        g.nv = nv;
+        b->h_grids[i] = g;
+        total += nv;
+    }
+    const size_t eb = wtype_bytes(wtype);
+    b->w_total_bytes = (size_t)total * eb;
+    cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
+    if (e == cudaSuccess && eb) e = cudaMalloc(&b->d_w, b->w_total_bytes);
+    if (e == cudaSuccess && eb) e = cudaMemcpyAsync(b->d_w, vertex_weights, b->w_total_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc batch"); }
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        b->h_grids[i].w = eb ? (const void *)((const char *)b->d_w + off * eb) : nullptr;
+        b->h_grids[i].status = b->d_status;
+        off += b->h_grids[i].nv;
+    }
+    if ((s = batch_finish(b, st))) { wect_batch_destroy(b); return s; }
+    uint64_t wmax = 255;
+    if (wtype == WECT_W_F32 || wtype == WECT_W_I64_FIXED) {
+        int *d_bad = nullptr;
+        e = cudaMalloc((void **)&d_bad, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.M.p, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, b->d_w, total, b->frac_bits, nullptr, b->ws.M.p, d_bad, st);
+        unsigned long long m = 0;
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&m, b->ws.M.p, sizeof m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (d_bad) cudaFree(d_bad);
+        if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "batch weights"); }
+        g_launches++;
+        if (bad) { wect_batch_destroy(b); return fail(WECT_ERR_INVALID_ARG, "vertex weights are not finite or too large"); }
+        wmax = m;
+    } else {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "sync"); }
+    }
+    if ((s = choose_cubical_mode(n, wtype, wmax, b->nsplit, b->climit, b->kflush))) { wect_batch_destroy(b); return s; }
+    *out = b;
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_batch_set_weights(wect_batch b, const void *w, wect_stream stream)
+{
+    if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
+    if (!b->d_w) return fail(WECT_ERR_UNSUPPORTED, "batch does not own its weights");
+    if (!w) return fail(WECT_ERR_INVALID_ARG, "weights is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    CK(cudaMemcpyAsync(b->d_w, w, b->w_total_bytes, cudaMemcpyDeviceToDevice, st), "copy weights");
+    KL(launch_weights_check(b->wtype, b->d_w, b->total_nv, b->frac_bits, b->climit >> b->n, b->d_status, st), "weights_check");
+    return WECT_OK;
+}
+
+extern "C" int wect_batch_count(wect_batch b) { return b ? b->count : 0; }
+extern "C" int64_t wect_batch_total_vertices(wect_batch b) { return b ? b->total_nv : 0; }
+
+static bool batch_shape(wect_batch b, int d, int T, CubShape &sh)
+{
+    auto it = b->tuned.find({d, T});
+    if (it != b->tuned.end())
+        return cub_shape(b->n, b->nsplit, d, T, b->maxL0, it->second.Dt, it->second.R, sh, it->second.dpl);
+    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, 0, 0, sh);
+}
+
+// Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
+// directly) when every complex fits one flush; otherwise row chunks balanced over the grid.
+static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, bool &direct, cudaStream_t st)
+{
+    int64_t maxnv = 0;
+    for (auto &g : b->h_grids) maxnv = std::max<int64_t>(maxnv, g.nv);
+    const int ntiles = (d + sh.Dt - 1) / sh.Dt;
+    direct = maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
+    auto key = std::make_tuple(d, T, sh.Dt, sh.R * 8 + sh.dpl, direct ? 1 : 0);
+    if (b->ws.items_key == key) return WECT_OK;
+    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, sh.R, 4 * sh.grid, direct);
+    wect_status s = upload_items(b->ws, items, st);
+    if (s) return s;
+    b->ws.items_key = key;
+    return WECT_OK;
+}
+
+static wect_status batch_enqueue(wect_batch b, const CubShape &sh, bool direct, const double *dirs, int d, int T,
+                                 double lo, double hi, int64_t *out, cudaStream_t st)
+{
+    CubLaunch L{b->n, b->nsplit, b->wtype, b->frac_bits, b->kflush, b->maxL0, b->climit, b->d_grids, &b->ws};
+    return enqueue_cubical_fwd(L, sh, b->ws.n_items, direct, dirs, d, T, lo, hi, false, (int64_t)b->count * d, out, st);
+}
+
+extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                          int64_t *out, wect_stream stream)
+{
+    if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
+    if (!dirs || !out) return fail(WECT_ERR_INVALID_ARG, "dirs/out is NULL");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    CubShape sh;
+    if (!batch_shape(b, d, T, sh)) return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
+    if ((s = ensure_common_ws(b->ws, T))) return s;
+    bool direct = false;
+    if ((s = batch_items(b, d, T, sh, direct, st))) return s;
+    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.R * 8 + sh.dpl);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        // capture the launch sequence once on a private stream, replay it on the caller's stream
+        CK(prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.smem), "prepare");
+        CK(cudaStreamSynchronize(st), "sync");
+        GraphEntry ge;
+        const int64_t before = g_launches.load();
+        CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        wect_status s2 = batch_enqueue(b, sh, direct, dirs, d, T, lo, hi, out, b->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &ge.graph);
+        if (s2) return s2;
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        ge.nodes = (int)(g_launches.load() - before);
+        g_launches -= ge.nodes;          // counted at each replay instead
+        if ((e = cudaGraphInstantiate(&ge.exec, ge.graph, 0)) != cudaSuccess) {
+            cudaGraphDestroy(ge.graph);
+            return cuda_fail(e, "instantiate");
+        }
+        it = b->graphs.emplace(key, ge).first;
+    }
+    {
+        ProfScope prof(st);
+        CK(cudaGraphLaunch(it->second.exec, st), "graph launch");
+    }
+    g_launches += it->second.nodes;
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                               int64_t *out, wect_stream stream)
+{
+    if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
+    if (!dirs || !out) return fail(WECT_ERR_INVALID_ARG, "dirs/out is NULL");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    CubShape sh;
+    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, 0, 0, sh)) return fail(WECT_ERR_UNSUPPORTED, "T too large");
+    if ((s = ensure_common_ws(b->ws, T))) return s;
+    // one item list per complex, concatenated; each complex launched on its own
+    std::vector<int> &starts = b->loop_starts;
+    auto key = std::make_tuple(d, T, sh.Dt, sh.R, 7);
+    if (b->ws.items_key != key) {
+        std::vector<WorkItem> all;
+        starts.assign(b->count + 1, 0);
+        for (int i = 0; i < b->count; ++i) {
+            std::vector<GridDesc> one(1, b->h_grids[i]);
+            std::vector<WorkItem> it = make_items(one, d, sh.Dt, sh.R, sh.grid, false);
+            for (auto &w : it) w.cx = i;
+            starts[i] = (int)all.size();
+            all.insert(all.end(), it.begin(), it.end());
+        }
+        starts[b->count] = (int)all.size();
+        if ((s = upload_items(b->ws, all, st))) return s;
+        b->ws.items_key = key;
+    }
+    KL(launch_setup_range_beta(lo, hi, 0, b->ws.M.p, T, b->ws.range.p, b->ws.beta.p, st), "setup_range_beta");
+    CK(cudaMemsetAsync(out, 0, (size_t)b->count * d * T * sizeof(int64_t), st), "memset");
+    for (int i = 0; i < b->count; ++i) {
+        CK(cudaMemsetAsync(b->ws.counter.p, 0, sizeof(int), st), "memset");
+        CubicalFwdArgs a{};
+        a.grids = b->d_grids;
+        a.items = b->ws.items.p + starts[i];
+        a.n_items = starts[i + 1] - starts[i];
+        a.counter = b->ws.counter.p;
+        a.dirs = dirs;
+        a.d = d;
+        a.T = T;
+        a.range = b->ws.range.p;
+        a.beta = b->ws.beta.p;
+        a.Dt = sh.Dt;
+        a.R = sh.R;
+        a.CP = cubical_fwd_pitch(b->n, sh.R, b->maxL0);
+        a.wt = b->wtype;
+        a.kflush = b->kflush;
+        a.frac_bits = b->frac_bits;
+        a.climit = b->climit;
+        a.direct = 0;
+        a.out = reinterpret_cast<unsigned long long *>(out);
+        KL(launch_cubical_fwd(b->n, b->nsplit, sh.dpl, a, std::max(1, std::min(sh.grid, a.n_items)), sh.smem, st), "fwd");
+        KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out) + (int64_t)i * d * T, d, T, st), "scan");
+    }
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_batch_backward(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                           const int64_t *dW, double scale, float *grad_w, wect_stream stream)
+{
+    if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
+    if (!dirs || !dW || !grad_w) return fail(WECT_ERR_INVALID_ARG, "NULL pointer argument");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    if (!std::isfinite(scale)) return fail(WECT_ERR_INVALID_ARG, "scale must be finite");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    return cubical_backward(b->d_grids, b->count, b->h_grids, b->n, b->wtype, b->frac_bits, b->total_nv, b->ws, dirs, d, T,
+                            lo, hi, dW, scale, grad_w, b->d_status, st);
+}
+
+extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                           int64_t *scratch_out, wect_stream stream)
+{
+    if (!b || !dirs || !scratch_out) return fail(WECT_ERR_INVALID_ARG, "NULL argument");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    if ((s = ensure_common_ws(b->ws, T))) return s;
+    const int warps = cubical_fwd_threads() / 32;
+    std::vector<std::tuple<int, int, int>> cands;
+    for (int dpl : {1, 2, 4})
+        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2)
+            for (int R = 1; R <= 64; R *= 2) cands.push_back({dpl, Dt, R});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    BatchConfig bc{0, 0};
+    for (auto [dpl, Dt, R] : cands) {
+        if (Dt > 2 * std::max(d, 32 * dpl)) continue;
+        CubShape sh;
+        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, Dt, R, sh, dpl) || sh.Dt != Dt || sh.R != R) continue;
+        bool direct = false;
+        if ((s = batch_items(b, d, T, sh, direct, st))) break;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(e0, st), "event");
+            if ((s = batch_enqueue(b, sh, direct, dirs, d, T, lo, hi, scratch_out, st))) break;
+            CK(cudaEventRecord(e1, st), "event");
+            CK(cudaEventSynchronize(e1), "event sync");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            ms_best = std::min(ms_best, ms);
+        }
+        if (s) break;
+        if (ms_best < best) {
+            best = ms_best;
+            bc = BatchConfig{dpl, Dt, R};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if (bc.Dt == 0) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+    b->tuned[{d, T}] = bc;
+    for (auto &kv : b->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    b->graphs.clear();
+    b->ws.items_key = std::make_tuple(-1, -1, -1, -1, -1);
+    return WECT_OK;
+}
+
+extern "C" void wect_batch_destroy(wect_batch b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    for (auto &kv : b->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_grids) cudaFree(b->d_grids);
+    if (b->d_status) cudaFree(b->d_status);
+    if (b->d_w) cudaFree(b->d_w);
+    b->ws.release();
+    delete b;
+}
+
+// ------------------------------------------------------------------ misc
+
+extern "C" const char *wect_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *wect_version(void) { return "wect-gb300 0.1 (sm_103a)"; }
+extern "C" int64_t wect_kernel_launch_count(void) { return g_launches.load(); }
+
+extern "C" wect_status wect_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_profile_read(double *kernel_ms, int64_t *launches)
+{
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        ev.swap(g_prof_events);
+    }
+    double tot = 0.0;
+    wect_status st = WECT_OK;
+    for (auto &p : ev) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.second);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.first, p.second);
+        if (e != cudaSuccess && st == WECT_OK) st = cuda_fail(e, "profile events");
+        tot += ms;
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    if (kernel_ms) *kernel_ms = tot;
+    if (launches) *launches = (int64_t)ev.size();
+    return st;
+}

@@ -1,0 +1,262 @@
+// wect_common.cu -- small kernels shared by every path: threshold table, prefix scans over
+// thresholds, direction grouping by octant, weight conversion and input validation.
+#include "wect_device.cuh"
+#include "wect_launch.h"
+
+namespace wect {
+
+// Resolve the threshold range and fill beta (Section 3: beta(q) = q 2M/(T-1) - M, here for a
+// range [lo, hi]; the default range is [-M, M] with M the largest |height|).
+//   range[0] = lo, range[1] = hi, range[2] = step = (hi - lo)/(T - 1); beta[q] = lo + q*step.
+__global__ void setup_range_beta_kernel(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
+                                        double *range, double *beta)
+{
+    if (use_default) {
+        const double M = __longlong_as_double((long long)*Mbits);
+        lo = -M;
+        hi = M;
+    }
+    const double step = __ddiv_rn(__dsub_rn(hi, lo), (double)(T - 1));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        range[0] = lo;
+        range[1] = hi;
+        range[2] = step;
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < T; q += gridDim.x * blockDim.x)
+        beta[q] = __dadd_rn(lo, __dmul_rn((double)q, step));
+}
+
+// Stable grouping of the directions by octant (bit a set when s_a > 0): perm lists the
+// directions octant by octant, octb[o] is where octant o starts.  One block.
+__global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, int *octb)
+{
+    __shared__ int cnt[8], start[9];
+    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int noct = 1 << n;
+    if (threadIdx.x == 0) {
+        for (int p = 0; p < d; ++p) {
+            int o = 0;
+            for (int a = 0; a < n; ++a)
+                if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
+            cnt[o]++;
+        }
+        start[0] = 0;
+        for (int o = 0; o < noct; ++o) start[o + 1] = start[o] + cnt[o];
+        for (int o = 0; o <= noct; ++o) octb[o] = start[o];
+        for (int p = 0; p < d; ++p) {
+            int o = 0;
+            for (int a = 0; a < n; ++a)
+                if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
+            perm[start[o]++] = p;
+        }
+    }
+}
+
+// In-place inclusive prefix sum of each row of an int64 [rows][T] table (Algorithm 1's final
+// cumulative sum): one warp per row, 32-wide shuffle scans with a running carry.
+__global__ void scan_rows_kernel(unsigned long long *data, int64_t rows, int T)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    long long *r = reinterpret_cast<long long *>(data) + row * T;
+    long long carry = 0;
+    for (int base = 0; base < T; base += 32) {
+        const int q = base + lane;
+        long long v = (q < T) ? r[q] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        v += carry;
+        if (q < T) r[q] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+}
+
+// Suffix sums S[q] = sum_{q' >= q} G[q'] of each row (the adjoint of the prefix scan).  The
+// adjoint later sums S over up to d directions in int64: entries with |S| > smax flag overflow.
+__global__ void suffix_rows_kernel(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const long long *a = reinterpret_cast<const long long *>(in) + row * T;
+    long long *o = reinterpret_cast<long long *>(out) + row * T;
+    long long carry = 0;
+    for (int top = T - 1; top >= 0; top -= 32) {
+        const int q = top - lane;
+        long long v = (q >= 0) ? a[q] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        v += carry;
+        if (q >= 0) {
+            o[q] = v;
+            if (status && (v > smax || v < -smax)) atomicOr(status, kStatusOverflow);
+        }
+        carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+}
+
+// Vertex weights to int64 fixed point, with max |w| and a flag for non-finite input.
+template <int WT>
+__global__ void weights_to_fixed_kernel(const void *w, int64_t nv, int frac_bits, int64_t *out,
+                                        unsigned long long *maxabs, int *bad)
+{
+    unsigned long long m = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        if (WT == WT_F32) {
+            const float x = ((const float *)w)[v];
+            if (!isfinite(x) || fabsf(x) >= 0x1p62f / ldexpf(1.0f, frac_bits)) {
+                atomicOr(bad, 1);
+                continue;
+            }
+        }
+        const int64_t f = load_weight_fixed<WT>(w, v, frac_bits);
+        if (out) out[v] = f;
+        const unsigned long long a = (unsigned long long)(f < 0 ? -f : f);
+        m = a > m ? a : m;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0 && maxabs) atomicMax(maxabs, m);
+}
+
+template <int WT>
+__global__ void weights_check_kernel(const void *w, int64_t nv, int frac_bits, int64_t limit, int *status)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        if (WT == WT_F32) {
+            const float x = ((const float *)w)[v];
+            if (!isfinite(x) || fabsf(x) >= 0x1p62f / ldexpf(1.0f, frac_bits)) {
+                atomicOr(status, kStatusOverflow);
+                continue;
+            }
+        }
+        const int64_t f = load_weight_fixed<WT>(w, v, frac_bits);
+        if (f > limit || f < -limit) atomicOr(status, kStatusOverflow);
+    }
+}
+
+__global__ void max_abs_f64_kernel(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits)
+{
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a = fabs(x[i * stride + offset]);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+        m = b > m ? b : m;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(Mbits, m);
+}
+
+__global__ void finite_check_kernel(const double *x, int64_t n, int *bad, int flag)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) atomicOr(bad, flag);
+}
+
+__global__ void index_check_kernel(const int32_t *idx, int64_t n, int64_t nv, int *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = idx[i];
+        if (v < 0 || (int64_t)v >= nv) atomicOr(bad, 1);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static unsigned grid_for(int64_t n, int threads, unsigned cap = 4096)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    return (unsigned)(g > cap ? cap : g);
+}
+
+cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
+                                    double *range, double *beta, cudaStream_t st)
+{
+    setup_range_beta_kernel<<<grid_for(T, 256, 64), 256, 0, st>>>(lo, hi, use_default, Mbits, T, range, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st)
+{
+    octant_sort_kernel<<<1, 32, 0, st>>>(n, dirs, d, perm, octb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st)
+{
+    const int wpb = 8;
+    scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(data, rows, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
+                               cudaStream_t st)
+{
+    const int wpb = 8;
+    suffix_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(in, out, rows, T, smax, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_to_fixed(int wt, const void *w, int64_t nv, int frac_bits, int64_t *out,
+                                    unsigned long long *maxabs, int *bad, cudaStream_t st)
+{
+    const unsigned g = grid_for(nv, 256);
+    switch (wt) {
+    case WT_U8: weights_to_fixed_kernel<WT_U8><<<g, 256, 0, st>>>(w, nv, frac_bits, out, maxabs, bad); break;
+    case WT_I64: weights_to_fixed_kernel<WT_I64><<<g, 256, 0, st>>>(w, nv, frac_bits, out, maxabs, bad); break;
+    case WT_F32: weights_to_fixed_kernel<WT_F32><<<g, 256, 0, st>>>(w, nv, frac_bits, out, maxabs, bad); break;
+    default: weights_to_fixed_kernel<WT_ONE><<<g, 256, 0, st>>>(w, nv, frac_bits, out, maxabs, bad); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_check(int wt, const void *w, int64_t nv, int frac_bits, int64_t limit, int *status,
+                                 cudaStream_t st)
+{
+    const unsigned g = grid_for(nv, 256);
+    switch (wt) {
+    case WT_U8: weights_check_kernel<WT_U8><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, status); break;
+    case WT_I64: weights_check_kernel<WT_I64><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, status); break;
+    case WT_F32: weights_check_kernel<WT_F32><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, status); break;
+    default: return cudaSuccess;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits,
+                               cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    max_abs_f64_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, stride, offset, Mbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finite_check(const double *x, int64_t n, int *bad, int flag, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    finite_check_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, bad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_index_check(const int32_t *idx, int64_t n, int64_t nv, int *bad, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    index_check_kernel<<<grid_for(n, 256), 256, 0, st>>>(idx, n, nv, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace wect

@@ -1,0 +1,781 @@
+// wect_cubical.cu -- stencil kernels for the WECT of full cubical grids (sm_103a).
+//
+// Lower-star values on a grid (Definition "Lower-Star Filtrations").  Along every grid axis
+// the float64 height h = fma(x0,s0, fma(x1,s1, x2*s2)) is monotone in the vertex index, with
+// the sign of s_a: each product is exact inside the fma, rounding is monotone, and each fma is
+// monotone in its addend.  So the maximum height over a cell (a box of the grid) is attained
+// at its "sign corner": the upper end on axes with s_a > 0, the lower end otherwise (ties give
+// equal heights, hence equal bins).  Grouping the cells by their sign corner turns the
+// per-cell scatter of Algorithm 1 into a per-vertex one:
+//     c_o(v) = sum over the 2^n cells whose sign corner under octant o is v of (-1)^dim w(cell),
+//     diff_p[bin_p(v)] += c_{o(p)}(v),
+// which is exact (integer sums) and touches 2^n times fewer elements.  The c_o(v) come from
+// each vertex's 3^n neighbourhood (the cell weight is the max of its vertex weights,
+// Figure 1), computed per tile in shared memory and reused by every direction of the tile.
+//
+// Forward kernel layout: lanes <-> directions (1, 2 or 4 per lane), rows of the grid walked in
+// order, per-CTA int32 histograms [T][Dt] in shared memory (a column per direction, so the 32
+// lanes of a red.shared hit 32 distinct banks).  Wide weights use two int32 planes (low 16
+// bits unsigned, high part signed) so that 65536 updates per entry cannot overflow.  Partial
+// histograms are flushed into the int64 output with global atomics (exact, order-free).
+#include "wect_device.cuh"
+#include "wect_launch.h"
+
+namespace wect {
+
+constexpr int kFwdThreads = 512;
+
+// ------------------------------------------------------------------ octant contributions
+
+// Vertex weight as a 32-bit fixed-point integer (the accumulator modes bound 2^n max|w| below
+// 2^31, checked at create / set-weights time).
+__device__ __forceinline__ int32_t load_w32(const void *w, int wt, int64_t v, int frac_bits)
+{
+    switch (wt) {
+    case WT_U8: return (int32_t)__ldg((const uint8_t *)w + v);
+    case WT_I64: return (int32_t)__ldg((const long long *)w + v);
+    case WT_F32: return __float2int_rn(ldexpf(__ldg((const float *)w + v), frac_bits));
+    default: return 1;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void octant_contribs(const GridDesc &g, int wt, int i0, int i1, int i2, int frac_bits,
+                                                int32_t *c /* [1 << N] */)
+{
+    constexpr int NOCT = 1 << N;
+    constexpr int NY = (N >= 2) ? 3 : 1;
+    constexpr int NZ = (N >= 3) ? 3 : 1;
+    const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+    const bool ok0[3] = {i0 > 0, true, i0 < L0 - 1};
+    const bool ok1[3] = {i1 > 0, true, i1 < L1 - 1};
+    const bool ok2[3] = {i2 > 0, true, i2 < L2 - 1};
+    const int64_t v = (int64_t)i0 + (int64_t)L0 * ((int64_t)i1 + (int64_t)L1 * i2);
+    // box maxima over the 3^n neighbourhood, axis by axis: A[z][y][x] = max over the box spanning
+    // v and v + (x-1, y-1, z-1)
+    int32_t A[NZ][NY][3];
+#pragma unroll
+    for (int z = 0; z < NZ; ++z)
+#pragma unroll
+        for (int y = 0; y < NY; ++y) {
+            int32_t w[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const int dy = (N >= 2) ? y - 1 : 0, dz = (N >= 3) ? z - 1 : 0;
+                const bool ok = ok0[x] && (N < 2 || ok1[y]) && (N < 3 || ok2[z]);
+                w[x] = (ok && wt != WT_ONE) ? load_w32(g.w, wt, v + (x - 1) + (int64_t)L0 * (dy + (int64_t)L1 * dz), frac_bits) : 1;
+            }
+            A[z][y][0] = max(w[0], w[1]);
+            A[z][y][1] = w[1];
+            A[z][y][2] = max(w[1], w[2]);
+        }
+    if (N >= 2) {
+#pragma unroll
+        for (int z = 0; z < NZ; ++z)
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const int32_t a0 = A[z][0][x], a1 = A[z][NY > 1 ? 1 : 0][x], a2 = A[z][NY > 2 ? 2 : 0][x];
+                A[z][0][x] = max(a0, a1);
+                if (NY > 2) A[z][2][x] = max(a1, a2);
+            }
+    }
+    if (N >= 3) {
+#pragma unroll
+        for (int y = 0; y < NY; ++y)
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const int32_t a0 = A[0][y][x], a1 = A[NZ > 1 ? 1 : 0][y][x], a2 = A[NZ > 2 ? 2 : 0][y][x];
+                A[0][y][x] = max(a0, a1);
+                if (NZ > 2) A[2][y][x] = max(a1, a2);
+            }
+    }
+#pragma unroll
+    for (int o = 0; o < NOCT; ++o) {
+        int32_t acc = 0;
+#pragma unroll
+        for (int e = 0; e < NOCT; ++e) {
+            int idx[3] = {1, 1, 1};
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                if ((e >> a) & 1) {
+                    const bool up = (o >> a) & 1;            // sign corner is the upper end: the cell reaches back
+                    idx[a] = up ? 0 : 2;
+                    ok = ok && (a == 0 ? ok0[idx[a]] : (a == 1 ? ok1[idx[a]] : ok2[idx[a]]));
+                }
+            }
+            const int32_t wb = A[N >= 3 ? idx[2] : 0][N >= 2 ? idx[1] : 0][idx[0]];
+            if (ok) acc += (__popc(e) & 1) ? -wb : wb;
+        }
+        c[o] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ forward helpers
+
+// Add the CTA's partial histograms into the int64 output block [d][T] and clear them.
+template <int NSPLIT>
+__device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int dtile, int d,
+                                              unsigned long long *out)
+{
+    const int hw = T * Dt;
+    for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
+        const int b = idx / Dt, col = idx - b * Dt;
+        const int p = dtile * Dt + col;
+        int64_t v;
+        if (NSPLIT == 1) {
+            v = hist[idx];
+        } else {
+            v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
+            hist[hw + idx] = 0;
+        }
+        hist[idx] = 0;
+        if (p < d && v != 0) atomicAdd(out + (int64_t)p * T + b, (unsigned long long)v);
+    }
+}
+
+// The item covered every row of its complex: the histogram is the complete difference table of
+// its directions.  Scan it over the thresholds (Algorithm 1's cumulative sum) and store the
+// transform directly (no atomics, no separate scan).
+template <int NSPLIT>
+__device__ __forceinline__ void cubical_flush_direct(int32_t *hist, int T, int Dt, int dtile, int d,
+                                                     unsigned long long *out)
+{
+    const int hw = T * Dt;
+    for (int col = threadIdx.x; col < Dt; col += blockDim.x) {
+        const int p = dtile * Dt + col;
+        long long acc = 0;
+        for (int q = 0; q < T; ++q) {
+            const int idx = q * Dt + col;
+            int64_t v;
+            if (NSPLIT == 1) {
+                v = hist[idx];
+            } else {
+                v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
+                hist[hw + idx] = 0;
+            }
+            hist[idx] = 0;
+            acc += v;
+            if (p < d) out[(int64_t)p * T + q] = (unsigned long long)acc;
+        }
+    }
+}
+
+// The float32 filter could not decide the bin of vertex (i0,i1,i2) in direction p: evaluate the
+// float64 height, find its exact bin and move the contribution if the tentative bin was wrong.
+template <int N, int NSPLIT>
+__device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDesc &g, int p, int i0, int i1, int i2,
+                                           int thi, int nr, int col, uint32_t histAddr, int Dt, uint32_t HOFF,
+                                           int cv, int hv)
+{
+    const int T = P.T;
+    int bt = thi - kMagicBits + nr;
+    bt = min(max(bt, 0), T - 1);
+    const double h = height3<N>(grid_coord(i0, g.L[0]), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]),
+                                P.dirs + (int64_t)p * N);
+    const int be = exact_bin_from(h, P.beta, T, bt);
+    if (be == bt) return;
+    const uint32_t at = histAddr + ((uint32_t)bt * (uint32_t)Dt + (uint32_t)col) * 4u;
+    const uint32_t ae = histAddr + ((uint32_t)be * (uint32_t)Dt + (uint32_t)col) * 4u;
+    if (NSPLIT == 1) {
+        red_shared_add(at, -cv);
+        red_shared_add(ae, cv);
+    } else {
+        red_shared_add_u32(at, (uint32_t)(-cv));
+        red_shared_add_u32(ae, (uint32_t)cv);
+        red_shared_add(at + HOFF, -hv);
+        red_shared_add(ae + HOFF, hv);
+    }
+}
+
+// One grid row for the DPL directions of each lane.  CLAMP selects the variant whose bins may
+// leave [0, T-1] (heights outside the threshold range); the other variant has been proven
+// in range for the whole row and skips the clamp.
+template <int N, int NSPLIT, int DPL, bool CLAMP>
+__device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *ctile, int CP, int rl,
+                                        int L0p, int L0, int i1, int i2, const float (&S0)[DPL],
+                                        const RowFilter (&rf)[DPL], const int (&oct)[DPL], const int (&col)[DPL],
+                                        int pbase, uint32_t histAddr, int Dt, uint32_t HOFF)
+{
+    constexpr int NOCT = 1 << N;
+    constexpr int U = (NSPLIT == 1 && DPL <= 2) ? 8 : 4;
+    const int T = P.T;
+    const uint32_t D4 = (uint32_t)Dt * 4u;
+    const uint32_t HIP = (uint32_t)(NOCT * CP) * 4u;        // byte offset of the high planes
+    uint32_t cb[DPL], hb[DPL];
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) {
+        cb[j] = smem_addr(ctile + oct[j] * CP + rl * L0p);
+        hb[j] = histAddr + (uint32_t)col[j] * 4u + (CLAMP ? 0u : (uint32_t)(rf[j].nr - kMagicBits) * D4);
+    }
+    const int LU = L0 - L0 % U;
+    float k0 = (float)(1 - L0);
+    for (int i0 = 0; i0 < LU; i0 += U) {
+        int cv[DPL][U], hv[DPL][U];
+#pragma unroll
+        for (int j = 0; j < DPL; ++j)
+#pragma unroll
+            for (int q = 0; q < U / 4; ++q) {
+                const int4 t = lds128(cb[j] + (uint32_t)(i0 + 4 * q) * 4u);
+                cv[j][4 * q] = t.x; cv[j][4 * q + 1] = t.y; cv[j][4 * q + 2] = t.z; cv[j][4 * q + 3] = t.w;
+                if (NSPLIT == 2) {
+                    const int4 h = lds128(cb[j] + HIP + (uint32_t)(i0 + 4 * q) * 4u);
+                    hv[j][4 * q] = h.x; hv[j][4 * q + 1] = h.y; hv[j][4 * q + 2] = h.z; hv[j][4 * q + 3] = h.w;
+                } else {
+                    hv[j][4 * q] = hv[j][4 * q + 1] = hv[j][4 * q + 2] = hv[j][4 * q + 3] = 0;
+                }
+            }
+        int bad = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float kk = k0 + 2.0f * (float)u;
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int tlo, thi;
+                filter_ceil(kk, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
+                bad |= tlo ^ thi;
+                uint32_t addr;
+                if (!CLAMP) {
+                    addr = (uint32_t)thi * D4 + hb[j];
+                } else {
+                    const int b = min(max(thi - kMagicBits + rf[j].nr, 0), T - 1);
+                    addr = hb[j] + (uint32_t)b * D4;
+                }
+                if (NSPLIT == 1) {
+                    red_shared_add(addr, cv[j][u]);
+                } else {
+                    red_shared_add_u32(addr, (uint32_t)cv[j][u]);
+                    red_shared_add(addr + HOFF, hv[j][u]);
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, bad != 0)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    int tlo, thi;
+                    filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
+                    if (tlo != thi)
+                        cubical_fixup<N, NSPLIT>(P, g, pbase + col[j], i0 + u, i1, i2, thi, rf[j].nr, col[j], histAddr,
+                                                 Dt, HOFF, cv[j][u], hv[j][u]);
+                }
+        }
+        k0 += 2.0f * (float)U;
+    }
+    // ragged tail of the row (fewer than U vertices), always clamped
+    for (int i0 = LU; i0 < L0; ++i0) {
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            const int cvs = ctile[oct[j] * CP + rl * L0p + i0];
+            const int hvs = (NSPLIT == 2) ? ctile[NOCT * CP + oct[j] * CP + rl * L0p + i0] : 0;
+            int tlo, thi;
+            filter_ceil(k0, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
+            const int b = min(max(thi - kMagicBits + rf[j].nr, 0), T - 1);
+            const uint32_t addr = histAddr + ((uint32_t)b * (uint32_t)Dt + (uint32_t)col[j]) * 4u;
+            if (NSPLIT == 1) {
+                red_shared_add(addr, cvs);
+            } else {
+                red_shared_add_u32(addr, (uint32_t)cvs);
+                red_shared_add(addr + HOFF, hvs);
+            }
+            if (tlo != thi)
+                cubical_fixup<N, NSPLIT>(P, g, pbase + col[j], i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF,
+                                         cvs, hvs);
+        }
+        k0 += 2.0f;
+    }
+}
+
+// ------------------------------------------------------------------ forward
+
+template <int N, int NSPLIT, int DPL>
+__global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
+{
+    constexpr int NOCT = 1 << N;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    const int T = P.T, Dt = P.Dt, R = P.R, CP = P.CP;
+    const int histWords = T * Dt;
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);                 // NSPLIT planes [T][Dt]
+    int32_t *ctile = hist + NSPLIT * histWords;                         // NSPLIT x NOCT planes of pitch CP
+    DirFilter *dirf = reinterpret_cast<DirFilter *>(ctile + NSPLIT * NOCT * CP);   // [Dt]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int WC = Dt / (32 * DPL);         // warps across the direction tile
+    const int RG = nwarps / WC;             // row groups
+    const int wcol = wid % WC, rgroup = wid / WC;
+    const uint32_t histAddr = smem_addr(hist);
+    const uint32_t HOFF = (uint32_t)histWords * 4u;
+    const double lo = P.range[0], hi = P.range[1], step = P.range[2];
+
+    for (int i = tid; i < NSPLIT * histWords; i += blockDim.x) hist[i] = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(P.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= P.n_items) break;
+        const WorkItem W = P.items[it];
+        const GridDesc g = P.grids[W.cx];
+        const int L0 = g.L[0], L1 = g.L[1];
+        const int L0p = (L0 + 3) & ~3;
+        const int pbase = W.dtile * Dt;
+
+        // ---- float32 filter constants of the tile's directions, one per column
+        for (int c = tid; c < Dt; c += blockDim.x) {
+            const int p = pbase + c;
+            double s[3] = {0.0, 0.0, 0.0};
+            DirFilter f;
+            if (p < P.d) {
+#pragma unroll
+                for (int a = 0; a < N; ++a) s[a] = P.dirs[(int64_t)p * N + a];
+                f = make_dir_filter<N>(s, g.L, lo, hi, step, T);
+            } else {        // idle column: parked on bin 1, never flushed
+                f.S0 = 0.f;
+                f.B1 = f.B2 = DS{0.f, 0.f};
+                f.C = DS{0.5f, 0.f};
+                f.eta = 0x1p-8f;
+                f.oct = 0;
+            }
+            dirf[c] = f;
+        }
+        int col[DPL];
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) col[j] = wcol * 32 * DPL + j * 32 + lane;
+        int since_flush = 0;
+
+        for (int rt = W.r0; rt < W.r1; rt += R) {
+            const int nrt = min(R, W.r1 - rt);
+            if (since_flush + nrt * L0 > P.kflush) {
+                __syncthreads();
+                cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
+                since_flush = 0;
+            }
+            __syncthreads();
+            // ---- octant contributions of the tile
+            for (int idx = tid; idx < nrt * L0p; idx += blockDim.x) {
+                const int rl = idx / L0p, i0 = idx - rl * L0p;
+                int32_t c[NOCT];
+                if (i0 < L0) {
+                    const int r = rt + rl;
+                    octant_contribs<N>(g, P.wt, i0, r % L1, r / L1, P.frac_bits, c);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < NOCT; ++o) c[o] = 0;
+                }
+#pragma unroll
+                for (int o = 0; o < NOCT; ++o) {
+                    const int32_t v = c[o];
+                    if ((int64_t)v > P.climit || (int64_t)v < -P.climit) atomicOr(g.status, kStatusOverflow);
+                    if (NSPLIT == 1) {
+                        ctile[o * CP + rl * L0p + i0] = v;
+                    } else {
+                        ctile[o * CP + rl * L0p + i0] = v & 0xFFFF;
+                        ctile[NOCT * CP + o * CP + rl * L0p + i0] = v >> 16;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- rows of the tile
+            for (int rl = rgroup; rl < nrt; rl += RG) {
+                const int r = rt + rl, i1 = r % L1, i2 = r / L1;
+                RowFilter rf[DPL];
+                float S0[DPL];
+                int oct[DPL];
+                bool clampRow = false;
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    const DirFilter f = dirf[col[j]];
+                    S0[j] = f.S0;
+                    oct[j] = f.oct;
+                    rf[j] = make_row_filter<N>(f, i1, i2, g.L);
+                    // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
+                    const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
+                    const float lowf = __fadd_rd(__fsub_rd(rf[j].Glo, A), (float)(rf[j].nr - 1));
+                    const float highf = __fadd_ru(__fadd_ru(rf[j].Ghi, A), (float)(rf[j].nr + 1));
+                    clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
+                }
+                if (__any_sync(0xffffffffu, clampRow))
+                    fwd_row<N, NSPLIT, DPL, true>(P, g, ctile, CP, rl, L0p, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
+                                                  Dt, HOFF);
+                else
+                    fwd_row<N, NSPLIT, DPL, false>(P, g, ctile, CP, rl, L0p, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
+                                                   Dt, HOFF);
+            }
+            since_flush += nrt * L0;
+        }
+        __syncthreads();
+        if (P.direct)
+            cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
+        else
+            cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
+    }
+}
+
+// ------------------------------------------------------------------ backward
+
+// Per-vertex octant sums of the suffix-scanned upstream gradient:
+//     Rv[v][o] = sum over directions p of octant o of S[p][bin_p(v)].
+// Lanes <-> vertices of a row; the direction loop is uniform across the warp and visits the
+// directions octant by octant (perm / octant bounds from the setup kernel).
+template <int N>
+__global__ void __launch_bounds__(256) cubical_bwd_rsum_kernel(const CubicalBwdArgs P)
+{
+    constexpr int NOCT = 1 << N;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = P.T, d = P.d;
+    const WorkItem W = P.items[blockIdx.x];
+    const GridDesc g = P.grids[W.cx];
+    const int L0 = g.L[0], L1 = g.L[1];
+    // shared: row filters [rows_per_block][d] (Glo, Ghi, nr) + S0 [d]
+    const int RB = P.R;
+    float *sGlo = reinterpret_cast<float *>(smem);
+    float *sGhi = sGlo + RB * d;
+    int *sNr = reinterpret_cast<int *>(sGhi + RB * d);
+    float *sS0 = reinterpret_cast<float *>(sNr + RB * d);
+    const double lo = P.range[0], hi = P.range[1], step = P.range[2];
+    const int64_t *S = P.S + (int64_t)W.cx * d * T;
+    const int segs = (L0 + 31) >> 5;
+    const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int rt = W.r0; rt < W.r1; rt += RB) {
+        const int nrt = min(RB, W.r1 - rt);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nrt * d; idx += blockDim.x) {
+            const int rl = idx / d, k = idx - rl * d;
+            const int p = P.perm[k];
+            double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a < N; ++a) s[a] = P.dirs[(int64_t)p * N + a];
+            const DirFilter F = make_dir_filter<N>(s, g.L, lo, hi, step, T);
+            const int r = rt + rl;
+            const RowFilter rf = make_row_filter<N>(F, r % L1, r / L1, g.L);
+            sGlo[rl * d + k] = rf.Glo;
+            sGhi[rl * d + k] = rf.Ghi;
+            sNr[rl * d + k] = rf.nr;
+            if (rl == 0) sS0[k] = F.S0;
+        }
+        __syncthreads();
+        for (int job = wid; job < nrt * segs; job += nwarps) {
+            const int rl = job / segs, seg = job - rl * segs;
+            const int i0 = seg * 32 + lane;
+            const bool live = i0 < L0;
+            const int r = rt + rl, i1 = r % L1, i2 = r / L1;
+            const float kk = (float)(2 * i0 - (L0 - 1));
+            int64_t acc[NOCT];
+#pragma unroll
+            for (int o = 0; o < NOCT; ++o) {
+                int64_t a = 0;
+                const int kb = P.octb[o], ke = P.octb[o + 1];
+                for (int k = kb; k < ke; ++k) {
+                    const float S0 = sS0[k];
+                    const float Glo = sGlo[rl * d + k], Ghi = sGhi[rl * d + k];
+                    const int nr = sNr[rl * d + k];
+                    int tlo, thi;
+                    filter_ceil(kk, S0, Glo, Ghi, tlo, thi);
+                    int b = thi - kMagicBits + nr;
+                    if (tlo != thi && live) {
+                        const int p = P.perm[k];
+                        const double *sp = P.dirs + (int64_t)p * N;
+                        const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]), sp);
+                        b = exact_bin_from(h, P.beta, T, b);
+                    }
+                    b = min(max(b, 0), T - 1);
+                    if (live) a += __ldg(S + (int64_t)P.perm[k] * T + b);
+                }
+                acc[o] = a;
+            }
+            if (live) {
+                const int64_t v = (int64_t)i0 + (int64_t)L0 * r;
+#pragma unroll
+                for (int o = 0; o < NOCT; ++o) P.Rv[(g.v_off + v) * NOCT + o] = acc[o];
+            }
+        }
+    }
+}
+
+// Route each cell's gradient to its heaviest vertex and sum exactly (128-bit):
+//     I_v = sum over cells s containing v whose heaviest vertex is v (ties -> lowest index) of
+//           (-1)^dim(s) sum_o Rv[corner_o(s)][o].
+template <int N, int WT>
+__global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwdArgs P)
+{
+    constexpr int NOCT = 1 << N;
+    constexpr int NB = (N == 1) ? 3 : (N == 2) ? 9 : 27;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // locate the complex by binary search on v_off
+    if (gid >= P.total_nv) return;
+    int lo_c = 0, hi_c = P.n_grids - 1;
+    while (lo_c < hi_c) {
+        const int mid = (lo_c + hi_c + 1) >> 1;
+        if (P.grids[mid].v_off <= gid) lo_c = mid; else hi_c = mid - 1;
+    }
+    const GridDesc g = P.grids[lo_c];
+    const int64_t v = gid - g.v_off;
+    const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+    const int i0 = (int)(v % L0), i1 = (int)((v / L0) % L1), i2 = (int)(v / ((int64_t)L0 * L1));
+    int64_t w[NB];
+    bool ok[NB];
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
+        const int j0 = i0 + dx, j1 = i1 + dy, j2 = i2 + dz;
+        ok[t] = j0 >= 0 && j0 < L0 && j1 >= 0 && j1 < L1 && j2 >= 0 && j2 < L2;
+        w[t] = ok[t] ? load_weight_fixed<WT>(g.w, v + dx + (int64_t)L0 * (dy + (int64_t)L1 * dz), P.frac_bits) : 0;
+    }
+    const int center = (N == 1) ? 1 : (N == 2) ? 4 : 13;
+    const int64_t wv = w[center];
+    int64_t Ihi = 0;
+    uint64_t Ilo = 0;
+    // each neighbour offset t defines the cell spanning v and v + delta(t)
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        if (!ok[t]) continue;
+        const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
+        const int dlt[3] = {dx, dy, dz};
+        // is v the heaviest vertex of the cell (ties to the lowest index)?
+        bool arg = true;
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int ux = u % 3 - 1, uy = (N >= 2) ? (u / 3) % 3 - 1 : 0, uz = (N >= 3) ? u / 9 - 1 : 0;
+            const int ud[3] = {ux, uy, uz};
+            bool inside = (u != center);
+#pragma unroll
+            for (int a = 0; a < N; ++a) inside = inside && (ud[a] == 0 || ud[a] == dlt[a]);
+            if (inside) {
+                // vertex u of the cell: offset ud; its flat index is below v iff the offset is lexicographically negative
+                const int64_t off = ux + (int64_t)L0 * (uy + (int64_t)L1 * uz);
+                if (w[u] > wv || (w[u] == wv && off < 0)) arg = false;
+            }
+        }
+        if (!arg) continue;
+        // g(cell) = sum_o Rv[sign corner under octant o][o]
+        int64_t gs = 0;
+#pragma unroll
+        for (int o = 0; o < NOCT; ++o) {
+            int cofs[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                if (dlt[a] != 0) {
+                    const bool up = (o >> a) & 1;
+                    // corner coordinate: upper end if up, lower end otherwise
+                    cofs[a] = up ? max(dlt[a], 0) : min(dlt[a], 0);
+                }
+            }
+            const int64_t cv = v + cofs[0] + (int64_t)L0 * (cofs[1] + (int64_t)L1 * cofs[2]);
+            gs += P.Rv[(g.v_off + cv) * NOCT + o];
+        }
+        int dimc = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a) dimc += (dlt[a] != 0);
+        if (dimc & 1) gs = -gs;
+        // 128-bit accumulate
+        const uint64_t old = Ilo;
+        Ilo += (uint64_t)gs;
+        Ihi += (gs < 0 ? -1 : 0) + (Ilo < old ? 1 : 0);
+    }
+    P.grad[g.v_off + v] = (float)(i128_to_double(Ihi, Ilo) * P.scale);
+}
+
+// ------------------------------------------------------------------ ECF on a grid (one vertex filter)
+
+// Bins of one caller-supplied vertex filter, exact float64 (binary search from a float guess).
+__global__ void filter_bins_kernel(const double *__restrict__ f, int64_t nv, const double *__restrict__ range,
+                                   const double *__restrict__ beta, int T, uint16_t *__restrict__ bins)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const double x = f[v];
+    const double lo = range[0], step = range[2];
+    int cand = 0;
+    if (step > 0.0) {
+        const double u = (x - lo) / step;
+        cand = (u < -1.0) ? 0 : (u > (double)T ? T - 1 : (int)ceil(u));
+    }
+    bins[v] = (uint16_t)exact_bin_from(x, beta, T, cand);
+}
+
+// Cells of a grid: each vertex owns the 2^n cells with it as the lower corner; the bin of a
+// cell is the max of its vertex bins (Eq. "msi"), its weight the max of its vertex weights.
+template <int N, int WT>
+__global__ void __launch_bounds__(256) cubical_ecf_kernel(const GridDesc *grids, const uint16_t *__restrict__ bins,
+                                                          int T, int weighted, int frac_bits,
+                                                          unsigned long long *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *h = reinterpret_cast<long long *>(smem);
+    for (int i = threadIdx.x; i < T; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const GridDesc g = grids[0];
+    const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int i0 = (int)(v % L0), i1 = (int)((v / L0) % L1), i2 = (int)(v / ((int64_t)L0 * L1));
+        for (int e = 0; e < (1 << N); ++e) {
+            const int e0 = e & 1, e1 = (e >> 1) & 1, e2 = (e >> 2) & 1;
+            if (i0 + e0 > L0 - 1 || (N >= 2 && i1 + e1 > L1 - 1) || (N >= 3 && i2 + e2 > L2 - 1)) continue;
+            int b = 0;
+            int64_t wm = INT64_MIN;
+            for (int s = 0; s < (1 << N); ++s) {
+                if (s & ~e) continue;
+                const int64_t u = v + (s & 1) + (int64_t)L0 * (((s >> 1) & 1) + (int64_t)L1 * ((s >> 2) & 1));
+                b = max(b, (int)bins[u]);
+                if (weighted) wm = max(wm, load_weight_fixed<WT>(g.w, u, frac_bits));
+            }
+            const int64_t w = weighted ? wm : 1;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&h[b]), (unsigned long long)((__popc(e) & 1) ? -w : w));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T; i += blockDim.x)
+        if (h[i]) atomicAdd(out + i, (unsigned long long)h[i]);
+}
+
+// ------------------------------------------------------------------ default range on a grid
+
+// M = max over directions and grid corners of |h|: h is monotone along every axis, so its
+// extremes over the grid are at corners.
+template <int N>
+__global__ void grid_max_abs_kernel(const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= d * (1 << N)) return;
+    const int p = t >> N, corner = t & ((1 << N) - 1);
+    const GridDesc g = grids[0];
+    const double x0 = grid_coord((corner & 1) ? g.L[0] - 1 : 0, g.L[0]);
+    const double x1 = grid_coord((corner & 2) ? g.L[1] - 1 : 0, g.L[1]);
+    const double x2 = grid_coord((corner & 4) ? g.L[2] - 1 : 0, g.L[2]);
+    const double h = fabs(height3<N>(x0, x1, x2, dirs + (int64_t)p * N));
+    atomicMax(Mbits, (unsigned long long)__double_as_longlong(h));
+}
+
+// ------------------------------------------------------------------ launchers
+
+// The dynamic shared-memory opt-in is set once per kernel instance and size (never inside a
+// stream capture once a size has been seen).
+template <int N, int NSPLIT, int DPL>
+static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
+{
+    static size_t done = 0;
+    if (smem > done) {
+        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        done = smem;
+    }
+    if (!launch) return cudaSuccess;
+    cubical_fwd_kernel<N, NSPLIT, DPL><<<grid, kFwdThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N, int NSPLIT>
+static cudaError_t launch_fwd_d(const CubicalFwdArgs &a, int dpl, int grid, size_t smem, cudaStream_t st, bool launch)
+{
+    switch (dpl) {
+    case 1: return launch_fwd_t<N, NSPLIT, 1>(a, grid, smem, st, launch);
+    case 2: return launch_fwd_t<N, NSPLIT, 2>(a, grid, smem, st, launch);
+    default: return launch_fwd_t<N, NSPLIT, 4>(a, grid, smem, st, launch);
+    }
+}
+
+static cudaError_t cubical_fwd_dispatch(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem,
+                                        cudaStream_t st, bool launch)
+{
+    if (n == 1) return nsplit == 1 ? launch_fwd_d<1, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<1, 2>(a, dpl, grid, smem, st, launch);
+    if (n == 2) return nsplit == 1 ? launch_fwd_d<2, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<2, 2>(a, dpl, grid, smem, st, launch);
+    return nsplit == 1 ? launch_fwd_d<3, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<3, 2>(a, dpl, grid, smem, st, launch);
+}
+
+cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    return cubical_fwd_dispatch(n, nsplit, dpl, a, grid, smem, st, true);
+}
+
+cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem)
+{
+    CubicalFwdArgs a{};
+    return cubical_fwd_dispatch(n, nsplit, dpl, a, 1, smem, nullptr, false);
+}
+
+int cubical_fwd_pitch(int n, int R, int maxL0)
+{
+    (void)n;
+    const int L0p = (maxL0 + 3) & ~3;
+    return ((R * L0p + 31) & ~31) + 4;        // words; odd multiple of 4 mod 32: octant planes on distinct bank groups
+}
+
+size_t cubical_fwd_smem(int n, int nsplit, int T, int Dt, int R, int maxL0)
+{
+    const int noct = 1 << n;
+    const int CP = cubical_fwd_pitch(n, R, maxL0);
+    return (size_t)nsplit * ((size_t)T * Dt + (size_t)noct * CP) * 4u + (size_t)Dt * sizeof(DirFilter);
+}
+
+int cubical_fwd_threads() { return kFwdThreads; }
+
+cudaError_t launch_cubical_bwd(int n, int wt, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
+{
+    cudaError_t e;
+    if (n == 1) {
+        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
+        if (e == cudaSuccess) cubical_bwd_rsum_kernel<1><<<n_items, 256, smem_rsum, st>>>(a);
+    } else if (n == 2) {
+        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
+        if (e == cudaSuccess) cubical_bwd_rsum_kernel<2><<<n_items, 256, smem_rsum, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
+        if (e == cudaSuccess) cubical_bwd_rsum_kernel<3><<<n_items, 256, smem_rsum, st>>>(a);
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int blocks = (int)((a.total_nv + 255) / 256);
+#define ROUTE(NN, W) cubical_bwd_route_kernel<NN, W><<<blocks, 256, 0, st>>>(a)
+    if (n == 1) { if (wt == WT_U8) ROUTE(1, WT_U8); else if (wt == WT_I64) ROUTE(1, WT_I64); else if (wt == WT_F32) ROUTE(1, WT_F32); else ROUTE(1, WT_ONE); }
+    else if (n == 2) { if (wt == WT_U8) ROUTE(2, WT_U8); else if (wt == WT_I64) ROUTE(2, WT_I64); else if (wt == WT_F32) ROUTE(2, WT_F32); else ROUTE(2, WT_ONE); }
+    else { if (wt == WT_U8) ROUTE(3, WT_U8); else if (wt == WT_I64) ROUTE(3, WT_I64); else if (wt == WT_F32) ROUTE(3, WT_F32); else ROUTE(3, WT_ONE); }
+#undef ROUTE
+    return cudaGetLastError();
+}
+
+size_t cubical_bwd_rsum_smem(int d, int R) { return (size_t)R * d * 12u + (size_t)d * 4u; }
+
+cudaError_t launch_cubical_ecf(int n, int wt, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
+                               int frac_bits, unsigned long long *out, int64_t nv, cudaStream_t st)
+{
+    const int blocks = (int)std::min<int64_t>((nv + 255) / 256, 1024);
+    const size_t sm = (size_t)T * 8u;
+    cudaError_t e = cudaSuccess;
+#define ECF(NN, W)                                                                                                    \
+    do {                                                                                                              \
+        e = cudaFuncSetAttribute(cubical_ecf_kernel<NN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
+        if (e == cudaSuccess) cubical_ecf_kernel<NN, W><<<blocks, 256, sm, st>>>(grids, bins, T, weighted, frac_bits, out); \
+    } while (0)
+    if (n == 1) { if (wt == WT_U8) ECF(1, WT_U8); else if (wt == WT_I64) ECF(1, WT_I64); else if (wt == WT_F32) ECF(1, WT_F32); else ECF(1, WT_ONE); }
+    else if (n == 2) { if (wt == WT_U8) ECF(2, WT_U8); else if (wt == WT_I64) ECF(2, WT_I64); else if (wt == WT_F32) ECF(2, WT_F32); else ECF(2, WT_ONE); }
+    else { if (wt == WT_U8) ECF(3, WT_U8); else if (wt == WT_I64) ECF(3, WT_I64); else if (wt == WT_F32) ECF(3, WT_F32); else ECF(3, WT_ONE); }
+#undef ECF
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
+                               uint16_t *bins, cudaStream_t st)
+{
+    filter_bins_kernel<<<(unsigned)((nv + 255) / 256), 256, 0, st>>>(f, nv, range, beta, T, bins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
+                                cudaStream_t st)
+{
+    const int tot = d * (1 << n);
+    const int blocks = (tot + 255) / 256;
+    if (n == 1) grid_max_abs_kernel<1><<<blocks, 256, 0, st>>>(grids, dirs, d, Mbits);
+    else if (n == 2) grid_max_abs_kernel<2><<<blocks, 256, 0, st>>>(grids, dirs, d, Mbits);
+    else grid_max_abs_kernel<3><<<blocks, 256, 0, st>>>(grids, dirs, d, Mbits);
+    return cudaGetLastError();
+}
+
+}  // namespace wect

@@ -1,0 +1,109 @@
+// wect_launch.h -- argument blocks and launchers shared between the kernels and the host API.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wect_device.cuh"
+
+namespace wect {
+
+struct CubicalFwdArgs {
+    const GridDesc *grids;
+    const WorkItem *items;
+    int n_items;
+    int *counter;                 // work-queue head, zero before the launch
+    const double *dirs;           // [d][n]
+    int d, T;
+    const double *range;          // [3] = lo, hi, step (resolved on the device)
+    const double *beta;           // [T]
+    int Dt, R;                    // direction-tile width, rows per shared-memory tile
+    int CP;                       // pitch (words) of the octant-contribution planes
+    int wt;                       // weight storage type
+    int kflush;                   // vertices per histogram flush
+    int frac_bits;
+    int64_t climit;               // largest |c_o(v)| the accumulator mode supports
+    int direct;                   // items cover whole complexes: scan in the CTA and store W
+    unsigned long long *out;      // int64 difference tables (or W when direct) [count][d][T]
+};
+
+struct CubicalBwdArgs {
+    const GridDesc *grids;
+    int n_grids;
+    const WorkItem *items;
+    const double *dirs;
+    int d, T;
+    const double *range;
+    const double *beta;
+    const int *perm;              // directions ordered by octant
+    const int *octb;              // [2^n + 1] octant bounds in perm
+    int R;
+    const int64_t *S;             // suffix sums [count][d][T]
+    int64_t *Rv;                  // [total_nv][2^n]
+    float *grad;                  // [total_nv]
+    double scale;
+    int frac_bits;
+    int64_t total_nv;
+};
+
+struct SimplexFwdArgs {
+    const int32_t *simp;          // [k][m] vertex ids (m = dim + 1)
+    const int64_t *sw;            // [k] fixed-point simplex weights
+    int64_t k;
+    int m;                        // vertices per simplex (1 = vertices themselves)
+    int sign;                     // (-1)^dim
+    const uint16_t *bins;         // [nv][Dt] vertex bins of the current direction tile
+    int Dt, dtile, d, T;
+    int64_t chunk;                // simplices per CTA work unit (<= flush bound)
+    unsigned long long *out;      // [d][T] int64
+};
+
+// cubical
+cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem);   // dynamic smem attribute, outside capture
+size_t cubical_fwd_smem(int n, int nsplit, int T, int Dt, int R, int maxL0);
+int cubical_fwd_pitch(int n, int R, int maxL0);
+int cubical_fwd_threads();
+cudaError_t launch_cubical_bwd(int n, int wt, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
+size_t cubical_bwd_rsum_smem(int d, int R);
+cudaError_t launch_cubical_ecf(int n, int wt, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
+                               int frac_bits, unsigned long long *out, int64_t nv, cudaStream_t st);
+cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
+                               uint16_t *bins, cudaStream_t st);
+cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
+                                cudaStream_t st);
+
+// simplicial
+cudaError_t launch_vertex_bins(int n, const double *coords, int64_t nv, const double *dirs, int d, int dtile, int Dt,
+                               int T, const double *range, const double *beta, uint16_t *bins, cudaStream_t st);
+cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st);
+size_t simplex_fwd_smem(int nsplit, int T, int Dt);
+cudaError_t launch_simplicial_max_abs(int n, const double *coords, int64_t nv, const double *dirs, int d,
+                                      unsigned long long *Mbits, float *Lbits_scratch, cudaStream_t st);
+cudaError_t launch_simplex_weights_max(const int32_t *simp, int64_t k, int m, const int64_t *vw, int64_t *sw,
+                                       cudaStream_t st);
+cudaError_t launch_simplicial_bwd(int n, const double *coords, int64_t nv, const int32_t *const *simp,
+                                  const int64_t *counts, int max_dim, const int64_t *vw, const double *dirs, int d,
+                                  int T, const double *range, const double *beta, const int64_t *S,
+                                  uint16_t *bins_all, unsigned long long *Iacc, float *grad, double scale,
+                                  cudaStream_t st);
+cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
+                               const uint16_t *bins, int T, unsigned long long *out, cudaStream_t st);
+
+// common
+cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
+                                    double *range, double *beta, cudaStream_t st);
+cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st);
+cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
+cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
+                               cudaStream_t st);
+cudaError_t launch_weights_to_fixed(int wt, const void *w, int64_t nv, int frac_bits, int64_t *out,
+                                    unsigned long long *maxabs, int *bad, cudaStream_t st);
+cudaError_t launch_weights_check(int wt, const void *w, int64_t nv, int frac_bits, int64_t limit, int *status,
+                                 cudaStream_t st);
+cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits,
+                               cudaStream_t st);
+cudaError_t launch_finite_check(const double *x, int64_t n, int *bad, int flag, cudaStream_t st);
+cudaError_t launch_index_check(const int32_t *idx, int64_t n, int64_t nv, int *bad, cudaStream_t st);
+
+}  // namespace wect
