@@ -186,8 +186,7 @@ struct wect_complex_s {
     int wtype = WECT_W_ONE;
     int frac_bits = 0;
     size_t wbytes = 0;             // bytes per raw vertex weight
-    void *d_w = nullptr;           // raw weights (cubical), owned unless borrowed
-    bool owns_w = true;
+    int32_t *d_w32 = nullptr;      // cubical: int32 fixed-point vertex weights read by the kernels
     int nsplit = 1;
     int64_t climit = 0;            // cubical: max |c_o(v)|; simplicial: max |w(s)|
     int kflush = 1 << 16;
@@ -213,7 +212,7 @@ struct GraphEntry {
 };
 
 struct BatchConfig {
-    int dpl = 0, Dt = 0, R = 0;
+    int dpl = 0, Dt = 0;
 };
 
 struct wect_batch_s {
@@ -230,8 +229,8 @@ struct wect_batch_s {
     std::vector<int64_t> v_off;
     GridDesc *d_grids = nullptr;
     int *d_status = nullptr;
-    void *d_w = nullptr;           // owned concatenated weights (create_cubical), else nullptr
-    size_t w_total_bytes = 0;
+    int32_t *d_w32 = nullptr;      // owned concatenated int32 weights (create_cubical), else nullptr
+    bool owns_w = false;
     Workspace ws;
     std::map<std::pair<int, int>, BatchConfig> tuned;    // (d, T) -> tile shape
     std::vector<int> loop_starts;                        // per-complex item ranges of the loop path
@@ -288,44 +287,32 @@ static wect_status choose_cubical_mode(int n, int wt, uint64_t wmax, int &nsplit
 // ------------------------------------------------------------------ tile shapes (cubical)
 
 struct CubShape {
-    int dpl, Dt, R, ctas_per_sm, grid;
+    int dpl, Dt, ctas_per_sm, grid;
     size_t smem;
 };
 
-// Directions per lane: 4 when the direction set fills a warp four times over, else fewer.
-static int pick_dpl(int d)
-{
-    if (d >= 128) return 4;
-    if (d >= 64) return 2;
-    return 1;
-}
-
-static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, int Dt_req, int R_req, CubShape &out, int dpl_req = 0)
+// Tile shape of the stencil kernel: the widest direction tile (fewest passes over the grid)
+// that fits shared memory, then the most directions per lane.  dpl_req / Dt_req pin a shape.
+static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0)
 {
     const int threads = cubical_fwd_threads();
     const int warps = threads / 32;
-    const int dpl = dpl_req > 0 ? dpl_req : pick_dpl(d);
-    const int per_warp = 32 * dpl;
     const size_t limit = smem_optin() - 1024;
-    int Dt_max = per_warp;
-    while (Dt_max < d && Dt_max * 2 <= per_warp * warps) Dt_max *= 2;
-    for (int Dt = (Dt_req > 0 ? Dt_req : Dt_max); Dt >= per_warp; Dt /= 2) {
-        const int WC = Dt / per_warp;
-        if (WC > warps || warps % WC) continue;
-        const int RG = warps / WC;
-        std::vector<int> Rs;
-        if (R_req > 0) Rs.push_back(R_req);
-        else for (int r = 4 * RG; r >= RG; r /= 2) Rs.push_back(r);
-        for (int R : Rs) {
-            if (R % RG) continue;
-            const size_t sm = cubical_fwd_smem(n, nsplit, T, Dt, R, maxL0);
+    int Dmax = 32;
+    while (Dmax < d && Dmax < 32 * 4 * warps) Dmax *= 2;
+    for (int Dt = (Dt_req > 0 ? Dt_req : Dmax); Dt >= 32; Dt /= 2) {
+        for (int dpl = 4; dpl >= 1; dpl /= 2) {
+            if (dpl_req > 0 && dpl != dpl_req) continue;
+            if (Dt % (32 * dpl)) continue;
+            const int WC = Dt / (32 * dpl);
+            if (WC > warps || warps % WC) continue;
+            if (dpl > 1 && Dt / dpl < 32) continue;
+            const size_t sm = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0);
             if (sm > limit) continue;
             out.dpl = dpl;
             out.Dt = Dt;
-            out.R = R;
             out.smem = sm;
-            const size_t per_sm = smem_per_sm();
-            int k = (int)(per_sm / (sm + 2048));
+            int k = (int)(smem_per_sm() / (sm + 2048));
             k = std::max(1, std::min(k, 2048 / threads));
             out.ctas_per_sm = k;
             out.grid = sm_count() * k;
@@ -336,8 +323,10 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, int Dt_req, in
     return false;
 }
 
-// Items for a set of grids: per complex, direction tiles x row chunks, largest first.
-static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int R, int target_items,
+// Items for a set of grids: per complex, direction tiles x row chunks, largest first.  An item
+// never holds more than kflush vertices (the int32 histogram bound); whole=true keeps one chunk
+// per complex (the caller has checked that every complex fits).
+static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int kflush, int target_items,
                                         bool whole)
 {
     const int ntiles = (d + Dt - 1) / Dt;
@@ -346,14 +335,15 @@ static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int 
     for (auto &g : grids) total_rows += g.rows;
     for (int c = 0; c < (int)grids.size(); ++c) {
         const GridDesc &g = grids[c];
+        const int max_rows = std::max(1, kflush / std::max(1, g.L[0]));
         int chunks = 1;
         if (!whole) {
             const double share = (double)g.rows / (double)std::max<int64_t>(total_rows, 1);
             chunks = (int)std::ceil(share * target_items / ntiles);
-            chunks = std::max(1, std::min(chunks, (g.rows + R - 1) / R));
+            chunks = std::max(chunks, (g.rows + max_rows - 1) / max_rows);
+            chunks = std::max(1, std::min(chunks, g.rows));
         }
-        int per = (g.rows + chunks - 1) / chunks;
-        per = ((per + R - 1) / R) * R;
+        const int per = (g.rows + chunks - 1) / chunks;
         for (int t = 0; t < ntiles; ++t)
             for (int r0 = 0; r0 < g.rows; r0 += per) {
                 WorkItem w{c, t, r0, std::min(g.rows, r0 + per)};
@@ -388,6 +378,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
         KL(launch_grid_max_abs(L.n, L.d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, ws.M.p, T, ws.range.p, ws.beta.p, st), "setup_range_beta");
+    KL(launch_octant_sort(L.n, dirs, d, ws.perm.p, ws.octb.p, st), "octant_sort");
     CK(cudaMemsetAsync(ws.counter.p, 0, sizeof(int), st), "memset");
     if (!direct) CK(cudaMemsetAsync(out, 0, (size_t)out_rows * T * sizeof(int64_t), st), "memset");
     CubicalFwdArgs a{};
@@ -401,11 +392,9 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.range = ws.range.p;
     a.beta = ws.beta.p;
     a.Dt = sh.Dt;
-    a.R = sh.R;
-    a.CP = cubical_fwd_pitch(L.n, sh.R, L.maxL0);
-    a.wt = L.wt;
+    a.CP = cubical_fwd_pitch(L.maxL0);
+    a.perm = ws.perm.p;
     a.kflush = L.kflush;
-    a.frac_bits = L.frac_bits;
     a.climit = L.climit;
     a.direct = direct ? 1 : 0;
     a.out = reinterpret_cast<unsigned long long *>(out);
@@ -424,8 +413,10 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     return WECT_OK;
 }
 
-static wect_status ensure_common_ws(Workspace &ws, int T)
+static wect_status ensure_common_ws(Workspace &ws, int T, int d = 1)
 {
+    CK(ws.perm.ensure((size_t)d), "alloc");
+    CK(ws.octb.ensure(9), "alloc");
     CK(ws.range.ensure(6), "alloc");
     CK(ws.beta.ensure((size_t)T), "alloc");
     CK(ws.M.ensure(2), "alloc");
@@ -486,43 +477,39 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     }
     auto cleanup = [&](wect_status st_) { wect_complex_destroy(c); return st_; };
     if ((s = new_status_word(&c->d_status))) return cleanup(s);
-    if (c->wbytes) {
-        cudaError_t e = cudaMalloc(&c->d_w, (size_t)nv * c->wbytes);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "alloc weights"));
-        e = cudaMemcpyAsync(c->d_w, vertex_weights, (size_t)nv * c->wbytes, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "copy weights"));
-    }
     if ((s = ensure_common_ws(c->ws, 2))) return cleanup(s);
-    int *d_bad = c->d_status;   // reuse the status word as a flag before it is published
+    cudaError_t e;
     uint64_t wmax = 255;
     if (wtype == WECT_W_F32 || wtype == WECT_W_I64_FIXED) {
-        cudaError_t e = cudaMemsetAsync(c->ws.M.p, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, c->d_w, nv, c->frac_bits, nullptr, c->ws.M.p, d_bad, st);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "weights_to_fixed"));
-        g_launches++;
+        int *d_bad = c->d_status;   // reuse the status word as a flag before it is published
         unsigned long long m = 0;
         int bad = 0;
-        e = cudaMemcpyAsync(&m, c->ws.M.p, sizeof m, cudaMemcpyDeviceToHost, st);
+        e = cudaMemsetAsync(c->ws.M.p, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, vertex_weights, nv, c->frac_bits, nullptr, c->ws.M.p, d_bad, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&m, c->ws.M.p, sizeof m, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "create sync"));
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "create weights"));
+        g_launches++;
         if (bad) return cleanup(fail(WECT_ERR_INVALID_ARG, "vertex weights are not finite or too large for int64 fixed point"));
         wmax = m;
-    } else {
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "create sync"));
     }
     if ((s = choose_cubical_mode(n, wtype, wmax, c->nsplit, c->climit, c->kflush))) return cleanup(s);
+    if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st))) return cleanup(cuda_fail(e, "memset"));
+    if ((e = cudaMalloc((void **)&c->d_w32, (size_t)nv * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc weights"));
+    if ((e = launch_weights_to_w32(wtype, vertex_weights, nv, c->frac_bits, c->climit >> n, c->d_w32, c->d_status, st)))
+        return cleanup(cuda_fail(e, "weights_to_w32"));
+    g_launches++;
     GridDesc g{};
-    g.w = c->d_w;
+    g.w = c->d_w32;
     for (int a = 0; a < 3; ++a) g.L[a] = c->L[a];
     g.rows = c->L[1] * c->L[2];
     g.nv = nv;
     g.v_off = 0;
     g.status = c->d_status;
-    cudaError_t e = cudaMalloc((void **)&c->d_grid, sizeof(GridDesc));
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    e = cudaMalloc((void **)&c->d_grid, sizeof(GridDesc));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload grid"));
     *out = c;
     return WECT_OK;
@@ -662,7 +649,7 @@ extern "C" void wect_complex_destroy(wect_complex c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
-    if (c->owns_w && c->d_w) cudaFree(c->d_w);
+    if (c->d_w32) cudaFree(c->d_w32);
     if (c->d_coords) cudaFree(c->d_coords);
     for (int i = 0; i < 4; ++i) {
         if (c->d_simp[i]) cudaFree(c->d_simp[i]);
@@ -710,8 +697,8 @@ extern "C" wect_status wect_complex_set_weights(wect_complex c, const void *w, w
     if (!w) return fail(WECT_ERR_INVALID_ARG, "weights is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
     if (c->kind == 0) {
-        CK(cudaMemcpyAsync(c->d_w, w, (size_t)c->nv * c->wbytes, cudaMemcpyDeviceToDevice, st), "copy weights");
-        KL(launch_weights_check(c->wtype, c->d_w, c->nv, c->frac_bits, c->climit >> c->n, c->d_status, st), "weights_check");
+        KL(launch_weights_to_w32(c->wtype, w, c->nv, c->frac_bits, c->climit >> c->n, c->d_w32, c->d_status, st),
+           "weights_to_w32");
         return WECT_OK;
     }
     if (c->sw_mode == WECT_SW_EXPLICIT) return fail(WECT_ERR_UNSUPPORTED, "set_weights on a complex with explicit simplex weights");
@@ -734,19 +721,20 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
                                    cudaStream_t st)
 {
     CubShape sh;
-    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], 0, 0, sh))
+    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh))
         return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
-    wect_status s = ensure_common_ws(c->ws, T);
+    if (c->L[0] > c->kflush) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
+    wect_status s = ensure_common_ws(c->ws, T, d);
     if (s) return s;
     const int rows = c->L[1] * c->L[2];
     const bool direct = false;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.R, sh.grid);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, sh.grid);
     if (c->ws.items_key != key) {
         std::vector<GridDesc> gv(1);
         gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
         gv[0].rows = rows;
         gv[0].nv = c->nv;
-        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, sh.R, sh.grid, false);
+        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, c->kflush, sh.grid, false);
         if ((s = upload_items(c->ws, items, st))) return s;
         c->ws.items_key = key;
     }
@@ -842,8 +830,8 @@ extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, 
     KL(launch_filter_bins(filter, c->nv, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, st), "filter_bins");
     CK(cudaMemsetAsync(out, 0, (size_t)T * sizeof(int64_t), st), "memset");
     if (c->kind == 0) {
-        KL(launch_cubical_ecf(c->n, weighted ? c->wtype : WECT_W_ONE, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0,
-                              c->frac_bits, reinterpret_cast<unsigned long long *>(out), c->nv, st),
+        KL(launch_cubical_ecf(c->n, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0,
+                              reinterpret_cast<unsigned long long *>(out), c->nv, st),
            "cubical_ecf");
     } else {
         for (int i = 0; i <= c->max_dim; ++i) {
@@ -865,7 +853,7 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
                                     int *status, cudaStream_t st)
 {
     if (range_is_default(lo, hi) && n_grids != 1) return fail(WECT_ERR_UNSUPPORTED, "default range in a batch");
-    wect_status s = ensure_common_ws(ws, T);
+    wect_status s = ensure_common_ws(ws, T, d);
     if (s) return s;
     const int noct = 1 << n;
     CK(ws.S.ensure((size_t)n_grids * d * T), "alloc S");
@@ -917,7 +905,7 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     a.total_nv = total_nv;
     {
         ProfScope prof(st);
-        KL(launch_cubical_bwd(n, wt, a, ws.n_items_bwd, sm, st), "cubical_bwd");
+        KL(launch_cubical_bwd(n, a, ws.n_items_bwd, sm, st), "cubical_bwd");
     }
     g_launches++;   // rsum + route
     return WECT_OK;
@@ -1010,7 +998,7 @@ extern "C" wect_status wect_batch_create(int count, const wect_complex *cxs, wec
     b->h_grids.resize(count);
     for (int i = 0; i < count; ++i) {
         GridDesc g{};
-        g.w = cxs[i]->d_w;
+        g.w = cxs[i]->d_w32;
         for (int a = 0; a < 3; ++a) g.L[a] = cxs[i]->L[a];
         g.rows = g.L[1] * g.L[2];
         g.nv = cxs[i]->nv;
@@ -1060,16 +1048,14 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
         b->h_grids[i] = g;
         total += nv;
     }
-    const size_t eb = wtype_bytes(wtype);
-    b->w_total_bytes = (size_t)total * eb;
     cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
-    if (e == cudaSuccess && eb) e = cudaMalloc(&b->d_w, b->w_total_bytes);
-    if (e == cudaSuccess && eb) e = cudaMemcpyAsync(b->d_w, vertex_weights, b->w_total_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_w32, (size_t)total * sizeof(int32_t));
     if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc batch"); }
+    b->owns_w = true;
     int64_t off = 0;
     for (int i = 0; i < count; ++i) {
-        b->h_grids[i].w = eb ? (const void *)((const char *)b->d_w + off * eb) : nullptr;
+        b->h_grids[i].w = b->d_w32 + off;
         b->h_grids[i].status = b->d_status;
         off += b->h_grids[i].nv;
     }
@@ -1080,7 +1066,7 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
         e = cudaMalloc((void **)&d_bad, sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.M.p, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, b->d_w, total, b->frac_bits, nullptr, b->ws.M.p, d_bad, st);
+        if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, vertex_weights, total, b->frac_bits, nullptr, b->ws.M.p, d_bad, st);
         unsigned long long m = 0;
         int bad = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&m, b->ws.M.p, sizeof m, cudaMemcpyDeviceToHost, st);
@@ -1091,11 +1077,12 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
         g_launches++;
         if (bad) { wect_batch_destroy(b); return fail(WECT_ERR_INVALID_ARG, "vertex weights are not finite or too large"); }
         wmax = m;
-    } else {
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "sync"); }
     }
     if ((s = choose_cubical_mode(n, wtype, wmax, b->nsplit, b->climit, b->kflush))) { wect_batch_destroy(b); return s; }
+    e = launch_weights_to_w32(wtype, vertex_weights, total, b->frac_bits, b->climit >> n, b->d_w32, b->d_status, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "weights_to_w32"); }
+    g_launches++;
     *out = b;
     return WECT_OK;
 }
@@ -1103,12 +1090,13 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
 extern "C" wect_status wect_batch_set_weights(wect_batch b, const void *w, wect_stream stream)
 {
     if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
-    if (!b->d_w) return fail(WECT_ERR_UNSUPPORTED, "batch does not own its weights");
+    if (!b->owns_w) return fail(WECT_ERR_UNSUPPORTED, "batch does not own its weights");
+    if (b->wtype == WECT_W_ONE) return WECT_OK;
     if (!w) return fail(WECT_ERR_INVALID_ARG, "weights is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
-    CK(cudaMemcpyAsync(b->d_w, w, b->w_total_bytes, cudaMemcpyDeviceToDevice, st), "copy weights");
-    KL(launch_weights_check(b->wtype, b->d_w, b->total_nv, b->frac_bits, b->climit >> b->n, b->d_status, st), "weights_check");
+    KL(launch_weights_to_w32(b->wtype, w, b->total_nv, b->frac_bits, b->climit >> b->n, b->d_w32, b->d_status, st),
+       "weights_to_w32");
     return WECT_OK;
 }
 
@@ -1118,9 +1106,8 @@ extern "C" int64_t wect_batch_total_vertices(wect_batch b) { return b ? b->total
 static bool batch_shape(wect_batch b, int d, int T, CubShape &sh)
 {
     auto it = b->tuned.find({d, T});
-    if (it != b->tuned.end())
-        return cub_shape(b->n, b->nsplit, d, T, b->maxL0, it->second.Dt, it->second.R, sh, it->second.dpl);
-    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, 0, 0, sh);
+    if (it != b->tuned.end()) return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt);
+    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh);
 }
 
 // Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
@@ -1131,9 +1118,9 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
     for (auto &g : b->h_grids) maxnv = std::max<int64_t>(maxnv, g.nv);
     const int ntiles = (d + sh.Dt - 1) / sh.Dt;
     direct = maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.R * 8 + sh.dpl, direct ? 1 : 0);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, direct ? 1 : 0);
     if (b->ws.items_key == key) return WECT_OK;
-    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, sh.R, 4 * sh.grid, direct);
+    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, b->kflush, 4 * sh.grid, direct);
     wect_status s = upload_items(b->ws, items, st);
     if (s) return s;
     b->ws.items_key = key;
@@ -1160,10 +1147,10 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
     if (!batch_shape(b, d, T, sh)) return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
-    if ((s = ensure_common_ws(b->ws, T))) return s;
+    if ((s = ensure_common_ws(b->ws, T, d))) return s;
     bool direct = false;
     if ((s = batch_items(b, d, T, sh, direct, st))) return s;
-    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.R * 8 + sh.dpl);
+    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.dpl);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         // capture the launch sequence once on a private stream, replay it on the caller's stream
@@ -1204,17 +1191,18 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
-    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, 0, 0, sh)) return fail(WECT_ERR_UNSUPPORTED, "T too large");
-    if ((s = ensure_common_ws(b->ws, T))) return s;
+    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "T too large");
+    if (b->maxL0 > b->kflush) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
+    if ((s = ensure_common_ws(b->ws, T, d))) return s;
     // one item list per complex, concatenated; each complex launched on its own
     std::vector<int> &starts = b->loop_starts;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.R, 7);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, 7);
     if (b->ws.items_key != key) {
         std::vector<WorkItem> all;
         starts.assign(b->count + 1, 0);
         for (int i = 0; i < b->count; ++i) {
             std::vector<GridDesc> one(1, b->h_grids[i]);
-            std::vector<WorkItem> it = make_items(one, d, sh.Dt, sh.R, sh.grid, false);
+            std::vector<WorkItem> it = make_items(one, d, sh.Dt, b->kflush, sh.grid, false);
             for (auto &w : it) w.cx = i;
             starts[i] = (int)all.size();
             all.insert(all.end(), it.begin(), it.end());
@@ -1224,6 +1212,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         b->ws.items_key = key;
     }
     KL(launch_setup_range_beta(lo, hi, 0, b->ws.M.p, T, b->ws.range.p, b->ws.beta.p, st), "setup_range_beta");
+    KL(launch_octant_sort(b->n, dirs, d, b->ws.perm.p, b->ws.octb.p, st), "octant_sort");
     CK(cudaMemsetAsync(out, 0, (size_t)b->count * d * T * sizeof(int64_t), st), "memset");
     for (int i = 0; i < b->count; ++i) {
         CK(cudaMemsetAsync(b->ws.counter.p, 0, sizeof(int), st), "memset");
@@ -1238,11 +1227,9 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.range = b->ws.range.p;
         a.beta = b->ws.beta.p;
         a.Dt = sh.Dt;
-        a.R = sh.R;
-        a.CP = cubical_fwd_pitch(b->n, sh.R, b->maxL0);
-        a.wt = b->wtype;
+        a.CP = cubical_fwd_pitch(b->maxL0);
+        a.perm = b->ws.perm.p;
         a.kflush = b->kflush;
-        a.frac_bits = b->frac_bits;
         a.climit = b->climit;
         a.direct = 0;
         a.out = reinterpret_cast<unsigned long long *>(out);
@@ -1277,21 +1264,20 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
-    if ((s = ensure_common_ws(b->ws, T))) return s;
+    if ((s = ensure_common_ws(b->ws, T, d))) return s;
     const int warps = cubical_fwd_threads() / 32;
-    std::vector<std::tuple<int, int, int>> cands;
+    std::vector<std::pair<int, int>> cands;
     for (int dpl : {1, 2, 4})
-        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2)
-            for (int R = 1; R <= 64; R *= 2) cands.push_back({dpl, Dt, R});
+        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2) cands.push_back({dpl, Dt});
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
     BatchConfig bc{0, 0};
-    for (auto [dpl, Dt, R] : cands) {
+    for (auto [dpl, Dt] : cands) {
         if (Dt > 2 * std::max(d, 32 * dpl)) continue;
         CubShape sh;
-        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, Dt, R, sh, dpl) || sh.Dt != Dt || sh.R != R) continue;
+        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt) || sh.Dt != Dt || sh.dpl != dpl) continue;
         bool direct = false;
         if ((s = batch_items(b, d, T, sh, direct, st))) break;
         float ms_best = 1e30f;
@@ -1307,7 +1293,7 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
         if (s) break;
         if (ms_best < best) {
             best = ms_best;
-            bc = BatchConfig{dpl, Dt, R};
+            bc = BatchConfig{dpl, Dt};
         }
     }
     cudaEventDestroy(e0);
@@ -1335,7 +1321,7 @@ extern "C" void wect_batch_destroy(wect_batch b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_status) cudaFree(b->d_status);
-    if (b->d_w) cudaFree(b->d_w);
+    if (b->owns_w && b->d_w32) cudaFree(b->d_w32);
     b->ws.release();
     delete b;
 }

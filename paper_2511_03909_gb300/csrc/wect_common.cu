@@ -26,30 +26,35 @@ __global__ void setup_range_beta_kernel(double lo, double hi, int use_default, c
         beta[q] = __dadd_rn(lo, __dmul_rn((double)q, step));
 }
 
-// Stable grouping of the directions by octant (bit a set when s_a > 0): perm lists the
-// directions octant by octant, octb[o] is where octant o starts.  One block.
+// Grouping of the directions by octant (bit a set when s_a > 0): perm lists the directions
+// octant by octant, octb[o] is where octant o starts.  One block; the order inside an octant
+// is arbitrary (every consumer sums integers, so results do not depend on it).
 __global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, int *octb)
 {
-    __shared__ int cnt[8], start[9];
-    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+    __shared__ int cnt[8], start[9], fill[8];
+    if (threadIdx.x < 8) {
+        cnt[threadIdx.x] = 0;
+        fill[threadIdx.x] = 0;
+    }
     __syncthreads();
-    const int noct = 1 << n;
+    for (int p = threadIdx.x; p < d; p += blockDim.x) {
+        int o = 0;
+        for (int a = 0; a < n; ++a)
+            if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
+        atomicAdd(&cnt[o], 1);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int p = 0; p < d; ++p) {
-            int o = 0;
-            for (int a = 0; a < n; ++a)
-                if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
-            cnt[o]++;
-        }
         start[0] = 0;
-        for (int o = 0; o < noct; ++o) start[o + 1] = start[o] + cnt[o];
-        for (int o = 0; o <= noct; ++o) octb[o] = start[o];
-        for (int p = 0; p < d; ++p) {
-            int o = 0;
-            for (int a = 0; a < n; ++a)
-                if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
-            perm[start[o]++] = p;
-        }
+        for (int o = 0; o < 8; ++o) start[o + 1] = start[o] + cnt[o];
+    }
+    __syncthreads();
+    if (threadIdx.x <= (1 << n)) octb[threadIdx.x] = start[threadIdx.x];
+    for (int p = threadIdx.x; p < d; p += blockDim.x) {
+        int o = 0;
+        for (int a = 0; a < n; ++a)
+            if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
+        perm[start[o] + atomicAdd(&fill[o], 1)] = p;
     }
 }
 
@@ -129,6 +134,26 @@ __global__ void weights_to_fixed_kernel(const void *w, int64_t nv, int frac_bits
     if ((threadIdx.x & 31) == 0 && maxabs) atomicMax(maxabs, m);
 }
 
+// Vertex weights to the int32 fixed-point copy the stencil kernels read; |w| above limit
+// (or non-finite input) sets the overflow bit of the status word.
+template <int WT>
+__global__ void weights_to_w32_kernel(const void *w, int64_t nv, int frac_bits, int64_t limit, int32_t *out, int *status)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        if (WT == WT_F32) {
+            const float x = ((const float *)w)[v];
+            if (!isfinite(x) || fabsf(x) >= 0x1p62f / ldexpf(1.0f, frac_bits)) {
+                atomicOr(status, kStatusOverflow);
+                out[v] = 0;
+                continue;
+            }
+        }
+        const int64_t f = load_weight_fixed<WT>(w, v, frac_bits);
+        if (f > limit || f < -limit) atomicOr(status, kStatusOverflow);
+        out[v] = (int32_t)f;
+    }
+}
+
 template <int WT>
 __global__ void weights_check_kernel(const void *w, int64_t nv, int frac_bits, int64_t limit, int *status)
 {
@@ -192,7 +217,7 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
 
 cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st)
 {
-    octant_sort_kernel<<<1, 32, 0, st>>>(n, dirs, d, perm, octb);
+    octant_sort_kernel<<<1, 1024, 0, st>>>(n, dirs, d, perm, octb);
     return cudaGetLastError();
 }
 
@@ -242,6 +267,19 @@ cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offse
 {
     if (n <= 0) return cudaSuccess;
     max_abs_f64_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, stride, offset, Mbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_to_w32(int wt, const void *w, int64_t nv, int frac_bits, int64_t limit, int32_t *out,
+                                  int *status, cudaStream_t st)
+{
+    const unsigned g = grid_for(nv, 256);
+    switch (wt) {
+    case WT_U8: weights_to_w32_kernel<WT_U8><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
+    case WT_I64: weights_to_w32_kernel<WT_I64><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
+    case WT_F32: weights_to_w32_kernel<WT_F32><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
+    default: weights_to_w32_kernel<WT_ONE><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
+    }
     return cudaGetLastError();
 }
 

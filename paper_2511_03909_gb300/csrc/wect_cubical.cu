@@ -27,21 +27,10 @@ constexpr int kFwdThreads = 512;
 
 // ------------------------------------------------------------------ octant contributions
 
-// Vertex weight as a 32-bit fixed-point integer (the accumulator modes bound 2^n max|w| below
-// 2^31, checked at create / set-weights time).
-__device__ __forceinline__ int32_t load_w32(const void *w, int wt, int64_t v, int frac_bits)
-{
-    switch (wt) {
-    case WT_U8: return (int32_t)__ldg((const uint8_t *)w + v);
-    case WT_I64: return (int32_t)__ldg((const long long *)w + v);
-    case WT_F32: return __float2int_rn(ldexpf(__ldg((const float *)w + v), frac_bits));
-    default: return 1;
-    }
-}
-
+// c_o(v) for every octant o from the int32 fixed-point weights of v's 3^n neighbourhood (the
+// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set).
 template <int N>
-__device__ __forceinline__ void octant_contribs(const GridDesc &g, int wt, int i0, int i1, int i2, int frac_bits,
-                                                int32_t *c /* [1 << N] */)
+__device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i1, int i2, int32_t *c /* [1 << N] */)
 {
     constexpr int NOCT = 1 << N;
     constexpr int NY = (N >= 2) ? 3 : 1;
@@ -63,7 +52,7 @@ __device__ __forceinline__ void octant_contribs(const GridDesc &g, int wt, int i
             for (int x = 0; x < 3; ++x) {
                 const int dy = (N >= 2) ? y - 1 : 0, dz = (N >= 3) ? z - 1 : 0;
                 const bool ok = ok0[x] && (N < 2 || ok1[y]) && (N < 3 || ok2[z]);
-                w[x] = (ok && wt != WT_ONE) ? load_w32(g.w, wt, v + (x - 1) + (int64_t)L0 * (dy + (int64_t)L1 * dz), frac_bits) : 1;
+                w[x] = ok ? __ldg(g.w + v + (x - 1) + (int64_t)L0 * (dy + (int64_t)L1 * dz)) : 0;
             }
             A[z][y][0] = max(w[0], w[1]);
             A[z][y][1] = w[1];
@@ -115,13 +104,13 @@ __device__ __forceinline__ void octant_contribs(const GridDesc &g, int wt, int i
 
 // Add the CTA's partial histograms into the int64 output block [d][T] and clear them.
 template <int NSPLIT>
-__device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int dtile, int d,
+__device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int dtile, int d, const int *perm,
                                               unsigned long long *out)
 {
     const int hw = T * Dt;
     for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
         const int b = idx / Dt, col = idx - b * Dt;
-        const int p = dtile * Dt + col;
+        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
         int64_t v;
         if (NSPLIT == 1) {
             v = hist[idx];
@@ -138,12 +127,12 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int 
 // its directions.  Scan it over the thresholds (Algorithm 1's cumulative sum) and store the
 // transform directly (no atomics, no separate scan).
 template <int NSPLIT>
-__device__ __forceinline__ void cubical_flush_direct(int32_t *hist, int T, int Dt, int dtile, int d,
+__device__ __forceinline__ void cubical_flush_direct(int32_t *hist, int T, int Dt, int dtile, int d, const int *perm,
                                                      unsigned long long *out)
 {
     const int hw = T * Dt;
     for (int col = threadIdx.x; col < Dt; col += blockDim.x) {
-        const int p = dtile * Dt + col;
+        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
         long long acc = 0;
         for (int q = 0; q < T; ++q) {
             const int idx = q * Dt + col;
@@ -192,10 +181,10 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
 // leave [0, T-1] (heights outside the threshold range); the other variant has been proven
 // in range for the whole row and skips the clamp.
 template <int N, int NSPLIT, int DPL, bool CLAMP>
-__device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *ctile, int CP, int rl,
-                                        int L0p, int L0, int i1, int i2, const float (&S0)[DPL],
-                                        const RowFilter (&rf)[DPL], const int (&oct)[DPL], const int (&col)[DPL],
-                                        int pbase, uint32_t histAddr, int Dt, uint32_t HOFF)
+__device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow, int CP, int L0,
+                                        int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
+                                        const int (&oct)[DPL], const int (&col)[DPL], int pbase, uint32_t histAddr,
+                                        int Dt, uint32_t HOFF)
 {
     constexpr int NOCT = 1 << N;
     constexpr int U = (NSPLIT == 1 && DPL <= 2) ? 8 : 4;
@@ -205,11 +194,25 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
     uint32_t cb[DPL], hb[DPL];
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
-        cb[j] = smem_addr(ctile + oct[j] * CP + rl * L0p);
+        cb[j] = smem_addr(crow + oct[j] * CP);
         hb[j] = histAddr + (uint32_t)col[j] * 4u + (CLAMP ? 0u : (uint32_t)(rf[j].nr - kMagicBits) * D4);
     }
     const int LU = L0 - L0 % U;
     float k0 = (float)(1 - L0);
+    // packed copies of the per-row constants for the f32x2 path
+    constexpr int NP = (DPL % 2 == 0) ? DPL / 2 : 1;
+    F2 S0p[NP], Glop[NP], Ghip[NP];
+    const F2 M2 = f2_pack(kMagic, kMagic);
+    if (DPL % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j + 1 < DPL; j += 2) {
+            S0p[j / 2] = f2_pack(S0[j], S0[j + 1]);
+            Glop[j / 2] = f2_pack(rf[j].Glo, rf[j + 1].Glo);
+            Ghip[j / 2] = f2_pack(rf[j].Ghi, rf[j + 1].Ghi);
+        }
+    }
+    F2 k02 = f2_pack(k0, k0);
+    const F2 step2 = f2_pack(2.0f * (float)U, 2.0f * (float)U);
     for (int i0 = 0; i0 < LU; i0 += U) {
         int cv[DPL][U], hv[DPL][U];
 #pragma unroll
@@ -228,17 +231,25 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
         int bad = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const float kk = k0 + 2.0f * (float)u;
+            int tlo[DPL], thi[DPL];
+            if (DPL % 2 == 0) {
+                // packed pairs of directions: one f32x2 instruction per step for two lanes' slots
+                const F2 kk2 = f2_add_rn(k02, f2_pack(2.0f * (float)u, 2.0f * (float)u));
+#pragma unroll
+                for (int j = 0; j < DPL; j += 2)
+                    filter_ceil2(kk2, S0p[j / 2], Glop[j / 2], Ghip[j / 2], M2, tlo[j], thi[j], tlo[j + 1], thi[j + 1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo[j], thi[j]);
+            }
 #pragma unroll
             for (int j = 0; j < DPL; ++j) {
-                int tlo, thi;
-                filter_ceil(kk, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
-                bad |= tlo ^ thi;
+                bad |= tlo[j] ^ thi[j];
                 uint32_t addr;
                 if (!CLAMP) {
-                    addr = (uint32_t)thi * D4 + hb[j];
+                    addr = (uint32_t)thi[j] * D4 + hb[j];
                 } else {
-                    const int b = min(max(thi - kMagicBits + rf[j].nr, 0), T - 1);
+                    const int b = min(max(thi[j] - kMagicBits + rf[j].nr, 0), T - 1);
                     addr = hb[j] + (uint32_t)b * D4;
                 }
                 if (NSPLIT == 1) {
@@ -257,18 +268,19 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                     int tlo, thi;
                     filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
                     if (tlo != thi)
-                        cubical_fixup<N, NSPLIT>(P, g, pbase + col[j], i0 + u, i1, i2, thi, rf[j].nr, col[j], histAddr,
-                                                 Dt, HOFF, cv[j][u], hv[j][u]);
+                        cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col[j]], i0 + u, i1, i2, thi, rf[j].nr, col[j],
+                                                 histAddr, Dt, HOFF, cv[j][u], hv[j][u]);
                 }
         }
         k0 += 2.0f * (float)U;
+        k02 = f2_add_rn(k02, step2);
     }
     // ragged tail of the row (fewer than U vertices), always clamped
     for (int i0 = LU; i0 < L0; ++i0) {
 #pragma unroll
         for (int j = 0; j < DPL; ++j) {
-            const int cvs = ctile[oct[j] * CP + rl * L0p + i0];
-            const int hvs = (NSPLIT == 2) ? ctile[NOCT * CP + oct[j] * CP + rl * L0p + i0] : 0;
+            const int cvs = crow[oct[j] * CP + i0];
+            const int hvs = (NSPLIT == 2) ? crow[NOCT * CP + oct[j] * CP + i0] : 0;
             int tlo, thi;
             filter_ceil(k0, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
             const int b = min(max(thi - kMagicBits + rf[j].nr, 0), T - 1);
@@ -280,8 +292,8 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                 red_shared_add(addr + HOFF, hvs);
             }
             if (tlo != thi)
-                cubical_fixup<N, NSPLIT>(P, g, pbase + col[j], i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF,
-                                         cvs, hvs);
+                cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col[j]], i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt,
+                                         HOFF, cvs, hvs);
         }
         k0 += 2.0f;
     }
@@ -289,22 +301,34 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
 
 // ------------------------------------------------------------------ forward
 
+// Barrier of the WC warps of one row group (warp-synchronous when the group is one warp).
+__device__ __forceinline__ void group_sync(int rgroup, int WC)
+{
+    if (WC == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + rgroup), "r"(WC * 32) : "memory");
+    }
+}
+
 template <int N, int NSPLIT, int DPL>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
 {
     constexpr int NOCT = 1 << N;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
-    const int T = P.T, Dt = P.Dt, R = P.R, CP = P.CP;
+    const int T = P.T, Dt = P.Dt, CP = P.CP;
     const int histWords = T * Dt;
-    int32_t *hist = reinterpret_cast<int32_t *>(smem);                 // NSPLIT planes [T][Dt]
-    int32_t *ctile = hist + NSPLIT * histWords;                         // NSPLIT x NOCT planes of pitch CP
-    DirFilter *dirf = reinterpret_cast<DirFilter *>(ctile + NSPLIT * NOCT * CP);   // [Dt]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int WC = Dt / (32 * DPL);         // warps across the direction tile
-    const int RG = nwarps / WC;             // row groups
+    const int WC = Dt / (32 * DPL);         // warps across the direction tile = warps of a row group
+    const int RG = nwarps / WC;             // row groups, each walking its own rows
     const int wcol = wid % WC, rgroup = wid / WC;
+    const int gtid = wcol * 32 + lane, gthreads = WC * 32;
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);                          // NSPLIT planes [T][Dt]
+    DirFilter *dirf = reinterpret_cast<DirFilter *>(hist + NSPLIT * histWords);  // [Dt]
+    const int rowbuf = NSPLIT * NOCT * CP;                                       // words of one row buffer
+    int32_t *cgrp = reinterpret_cast<int32_t *>(dirf + Dt) + rgroup * 2 * rowbuf;  // this group's 2 buffers
     const uint32_t histAddr = smem_addr(hist);
     const uint32_t HOFF = (uint32_t)histWords * 4u;
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
@@ -320,12 +344,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         const WorkItem W = P.items[it];
         const GridDesc g = P.grids[W.cx];
         const int L0 = g.L[0], L1 = g.L[1];
-        const int L0p = (L0 + 3) & ~3;
         const int pbase = W.dtile * Dt;
 
         // ---- float32 filter constants of the tile's directions, one per column
         for (int c = tid; c < Dt; c += blockDim.x) {
-            const int p = pbase + c;
+            const int p = (pbase + c < P.d) ? P.perm[pbase + c] : P.d;
             double s[3] = {0.0, 0.0, 0.0};
             DirFilter f;
             if (p < P.d) {
@@ -341,77 +364,60 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
             }
             dirf[c] = f;
         }
+        __syncthreads();
         int col[DPL];
 #pragma unroll
         for (int j = 0; j < DPL; ++j) col[j] = wcol * 32 * DPL + j * 32 + lane;
-        int since_flush = 0;
 
-        for (int rt = W.r0; rt < W.r1; rt += R) {
-            const int nrt = min(R, W.r1 - rt);
-            if (since_flush + nrt * L0 > P.kflush) {
-                __syncthreads();
-                cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
-                since_flush = 0;
-            }
-            __syncthreads();
-            // ---- octant contributions of the tile
-            for (int idx = tid; idx < nrt * L0p; idx += blockDim.x) {
-                const int rl = idx / L0p, i0 = idx - rl * L0p;
+        // ---- each row group walks rows r0 + rgroup, r0 + rgroup + RG, ... with a double-buffered
+        // row of octant contributions (one group barrier per row, no block-wide barrier)
+        int parity = 0;
+        for (int r = W.r0 + rgroup; r < W.r1; r += RG, parity ^= 1) {
+            int32_t *crow = cgrp + parity * rowbuf;
+            const int i1 = r % L1, i2 = r / L1;
+            for (int i0 = gtid; i0 < L0; i0 += gthreads) {
                 int32_t c[NOCT];
-                if (i0 < L0) {
-                    const int r = rt + rl;
-                    octant_contribs<N>(g, P.wt, i0, r % L1, r / L1, P.frac_bits, c);
-                } else {
-#pragma unroll
-                    for (int o = 0; o < NOCT; ++o) c[o] = 0;
-                }
+                octant_contribs<N>(g, i0, i1, i2, c);
 #pragma unroll
                 for (int o = 0; o < NOCT; ++o) {
                     const int32_t v = c[o];
                     if ((int64_t)v > P.climit || (int64_t)v < -P.climit) atomicOr(g.status, kStatusOverflow);
                     if (NSPLIT == 1) {
-                        ctile[o * CP + rl * L0p + i0] = v;
+                        crow[o * CP + i0] = v;
                     } else {
-                        ctile[o * CP + rl * L0p + i0] = v & 0xFFFF;
-                        ctile[NOCT * CP + o * CP + rl * L0p + i0] = v >> 16;
+                        crow[o * CP + i0] = v & 0xFFFF;
+                        crow[NOCT * CP + o * CP + i0] = v >> 16;
                     }
                 }
             }
-            __syncthreads();
+            group_sync(rgroup, WC);
 
-            // ---- rows of the tile
-            for (int rl = rgroup; rl < nrt; rl += RG) {
-                const int r = rt + rl, i1 = r % L1, i2 = r / L1;
-                RowFilter rf[DPL];
-                float S0[DPL];
-                int oct[DPL];
-                bool clampRow = false;
+            RowFilter rf[DPL];
+            float S0[DPL];
+            int oct[DPL];
+            bool clampRow = false;
 #pragma unroll
-                for (int j = 0; j < DPL; ++j) {
-                    const DirFilter f = dirf[col[j]];
-                    S0[j] = f.S0;
-                    oct[j] = f.oct;
-                    rf[j] = make_row_filter<N>(f, i1, i2, g.L);
-                    // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
-                    const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
-                    const float lowf = __fadd_rd(__fsub_rd(rf[j].Glo, A), (float)(rf[j].nr - 1));
-                    const float highf = __fadd_ru(__fadd_ru(rf[j].Ghi, A), (float)(rf[j].nr + 1));
-                    clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
-                }
-                if (__any_sync(0xffffffffu, clampRow))
-                    fwd_row<N, NSPLIT, DPL, true>(P, g, ctile, CP, rl, L0p, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
-                                                  Dt, HOFF);
-                else
-                    fwd_row<N, NSPLIT, DPL, false>(P, g, ctile, CP, rl, L0p, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
-                                                   Dt, HOFF);
+            for (int j = 0; j < DPL; ++j) {
+                const DirFilter f = dirf[col[j]];
+                S0[j] = f.S0;
+                oct[j] = f.oct;
+                rf[j] = make_row_filter<N>(f, i1, i2, g.L);
+                // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
+                const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
+                const float lowf = __fadd_rd(__fsub_rd(rf[j].Glo, A), (float)(rf[j].nr - 1));
+                const float highf = __fadd_ru(__fadd_ru(rf[j].Ghi, A), (float)(rf[j].nr + 1));
+                clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
             }
-            since_flush += nrt * L0;
+            if (__any_sync(0xffffffffu, clampRow))
+                fwd_row<N, NSPLIT, DPL, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF);
+            else
+                fwd_row<N, NSPLIT, DPL, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF);
         }
         __syncthreads();
         if (P.direct)
-            cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
+            cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, P.out + (int64_t)W.cx * P.d * T);
         else
-            cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.out + (int64_t)W.cx * P.d * T);
+            cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, P.out + (int64_t)W.cx * P.d * T);
     }
 }
 
@@ -500,7 +506,7 @@ __global__ void __launch_bounds__(256) cubical_bwd_rsum_kernel(const CubicalBwdA
 // Route each cell's gradient to its heaviest vertex and sum exactly (128-bit):
 //     I_v = sum over cells s containing v whose heaviest vertex is v (ties -> lowest index) of
 //           (-1)^dim(s) sum_o Rv[corner_o(s)][o].
-template <int N, int WT>
+template <int N>
 __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwdArgs P)
 {
     constexpr int NOCT = 1 << N;
@@ -524,7 +530,7 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
         const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
         const int j0 = i0 + dx, j1 = i1 + dy, j2 = i2 + dz;
         ok[t] = j0 >= 0 && j0 < L0 && j1 >= 0 && j1 < L1 && j2 >= 0 && j2 < L2;
-        w[t] = ok[t] ? load_weight_fixed<WT>(g.w, v + dx + (int64_t)L0 * (dy + (int64_t)L1 * dz), P.frac_bits) : 0;
+        w[t] = ok[t] ? (int64_t)__ldg(g.w + v + dx + (int64_t)L0 * (dy + (int64_t)L1 * dz)) : 0;
     }
     const int center = (N == 1) ? 1 : (N == 2) ? 4 : 13;
     const int64_t wv = w[center];
@@ -600,10 +606,9 @@ __global__ void filter_bins_kernel(const double *__restrict__ f, int64_t nv, con
 
 // Cells of a grid: each vertex owns the 2^n cells with it as the lower corner; the bin of a
 // cell is the max of its vertex bins (Eq. "msi"), its weight the max of its vertex weights.
-template <int N, int WT>
+template <int N>
 __global__ void __launch_bounds__(256) cubical_ecf_kernel(const GridDesc *grids, const uint16_t *__restrict__ bins,
-                                                          int T, int weighted, int frac_bits,
-                                                          unsigned long long *__restrict__ out)
+                                                          int T, int weighted, unsigned long long *__restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *h = reinterpret_cast<long long *>(smem);
@@ -622,7 +627,7 @@ __global__ void __launch_bounds__(256) cubical_ecf_kernel(const GridDesc *grids,
                 if (s & ~e) continue;
                 const int64_t u = v + (s & 1) + (int64_t)L0 * (((s >> 1) & 1) + (int64_t)L1 * ((s >> 2) & 1));
                 b = max(b, (int)bins[u]);
-                if (weighted) wm = max(wm, load_weight_fixed<WT>(g.w, u, frac_bits));
+                if (weighted) wm = max(wm, (int64_t)__ldg(g.w + u));
             }
             const int64_t w = weighted ? wm : 1;
             atomicAdd(reinterpret_cast<unsigned long long *>(&h[b]), (unsigned long long)((__popc(e) & 1) ? -w : w));
@@ -699,62 +704,59 @@ cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem)
     return cubical_fwd_dispatch(n, nsplit, dpl, a, 1, smem, nullptr, false);
 }
 
-int cubical_fwd_pitch(int n, int R, int maxL0)
+int cubical_fwd_pitch(int maxL0)
 {
-    (void)n;
     const int L0p = (maxL0 + 3) & ~3;
-    return ((R * L0p + 31) & ~31) + 4;        // words; odd multiple of 4 mod 32: octant planes on distinct bank groups
+    return ((L0p + 31) & ~31) + 4;        // words; = 4 mod 32: octant planes on distinct bank groups
 }
 
-size_t cubical_fwd_smem(int n, int nsplit, int T, int Dt, int R, int maxL0)
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0)
 {
     const int noct = 1 << n;
-    const int CP = cubical_fwd_pitch(n, R, maxL0);
-    return (size_t)nsplit * ((size_t)T * Dt + (size_t)noct * CP) * 4u + (size_t)Dt * sizeof(DirFilter);
+    const int WC = Dt / (32 * dpl);
+    const int RG = (kFwdThreads / 32) / WC;
+    const size_t rowbuf = (size_t)nsplit * noct * cubical_fwd_pitch(maxL0);
+    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * 2 * rowbuf * 4u;
 }
 
 int cubical_fwd_threads() { return kFwdThreads; }
 
-cudaError_t launch_cubical_bwd(int n, int wt, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
+cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
 {
     cudaError_t e;
-    if (n == 1) {
-        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
-        if (e == cudaSuccess) cubical_bwd_rsum_kernel<1><<<n_items, 256, smem_rsum, st>>>(a);
-    } else if (n == 2) {
-        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
-        if (e == cudaSuccess) cubical_bwd_rsum_kernel<2><<<n_items, 256, smem_rsum, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rsum);
-        if (e == cudaSuccess) cubical_bwd_rsum_kernel<3><<<n_items, 256, smem_rsum, st>>>(a);
-    }
-    if (e != cudaSuccess) return e;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int blocks = (int)((a.total_nv + 255) / 256);
-#define ROUTE(NN, W) cubical_bwd_route_kernel<NN, W><<<blocks, 256, 0, st>>>(a)
-    if (n == 1) { if (wt == WT_U8) ROUTE(1, WT_U8); else if (wt == WT_I64) ROUTE(1, WT_I64); else if (wt == WT_F32) ROUTE(1, WT_F32); else ROUTE(1, WT_ONE); }
-    else if (n == 2) { if (wt == WT_U8) ROUTE(2, WT_U8); else if (wt == WT_I64) ROUTE(2, WT_I64); else if (wt == WT_F32) ROUTE(2, WT_F32); else ROUTE(2, WT_ONE); }
-    else { if (wt == WT_U8) ROUTE(3, WT_U8); else if (wt == WT_I64) ROUTE(3, WT_I64); else if (wt == WT_F32) ROUTE(3, WT_F32); else ROUTE(3, WT_ONE); }
-#undef ROUTE
+#define BWD(NN)                                                                                                \
+    do {                                                                                                       \
+        e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)smem_rsum);                                                              \
+        if (e != cudaSuccess) return e;                                                                        \
+        cubical_bwd_rsum_kernel<NN><<<n_items, 256, smem_rsum, st>>>(a);                                       \
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;                                                 \
+        cubical_bwd_route_kernel<NN><<<blocks, 256, 0, st>>>(a);                                               \
+    } while (0)
+    if (n == 1) BWD(1);
+    else if (n == 2) BWD(2);
+    else BWD(3);
+#undef BWD
     return cudaGetLastError();
 }
 
 size_t cubical_bwd_rsum_smem(int d, int R) { return (size_t)R * d * 12u + (size_t)d * 4u; }
 
-cudaError_t launch_cubical_ecf(int n, int wt, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
-                               int frac_bits, unsigned long long *out, int64_t nv, cudaStream_t st)
+cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
+                               unsigned long long *out, int64_t nv, cudaStream_t st)
 {
     const int blocks = (int)std::min<int64_t>((nv + 255) / 256, 1024);
     const size_t sm = (size_t)T * 8u;
     cudaError_t e = cudaSuccess;
-#define ECF(NN, W)                                                                                                    \
-    do {                                                                                                              \
-        e = cudaFuncSetAttribute(cubical_ecf_kernel<NN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);    \
-        if (e == cudaSuccess) cubical_ecf_kernel<NN, W><<<blocks, 256, sm, st>>>(grids, bins, T, weighted, frac_bits, out); \
+#define ECF(NN)                                                                                               \
+    do {                                                                                                      \
+        e = cudaFuncSetAttribute(cubical_ecf_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e == cudaSuccess) cubical_ecf_kernel<NN><<<blocks, 256, sm, st>>>(grids, bins, T, weighted, out);  \
     } while (0)
-    if (n == 1) { if (wt == WT_U8) ECF(1, WT_U8); else if (wt == WT_I64) ECF(1, WT_I64); else if (wt == WT_F32) ECF(1, WT_F32); else ECF(1, WT_ONE); }
-    else if (n == 2) { if (wt == WT_U8) ECF(2, WT_U8); else if (wt == WT_I64) ECF(2, WT_I64); else if (wt == WT_F32) ECF(2, WT_F32); else ECF(2, WT_ONE); }
-    else { if (wt == WT_U8) ECF(3, WT_U8); else if (wt == WT_I64) ECF(3, WT_I64); else if (wt == WT_F32) ECF(3, WT_F32); else ECF(3, WT_ONE); }
+    if (n == 1) ECF(1);
+    else if (n == 2) ECF(2);
+    else ECF(3);
 #undef ECF
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

@@ -33,7 +33,7 @@ constexpr int WT_ONE = 3;
 
 // One cubical grid as seen by the kernels.
 struct GridDesc {
-    const void *w;       // raw vertex weights (type given by the launch), nullptr for WT_ONE
+    const int32_t *w;    // vertex weights as int32 fixed point (all ones when unweighted)
     int L[3];            // axis lengths, 1 for unused axes
     int rows;            // L[1] * L[2]
     int64_t nv;          // vertex count
@@ -183,6 +183,38 @@ __device__ __forceinline__ void filter_ceil(float k0, float S0, float Glo, float
     thi = __float_as_int(__fadd_ru(uh, kMagic));
 }
 
+// Two directions at once with the packed float32 pipe (sm_100+ f32x2): element-wise the same
+// IEEE operations, with the same directed roundings, as filter_ceil.
+struct F2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ F2 f2_pack(float a, float b)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ F2 f2_add_rn(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ void filter_ceil2(F2 k0, F2 S0, F2 Glo, F2 Ghi, F2 M, int &tlo_a, int &thi_a, int &tlo_b,
+                                             int &thi_b)
+{
+    unsigned long long ul, uh, tl, th;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(ul) : "l"(k0.v), "l"(S0.v), "l"(Glo.v));
+    asm("fma.rp.f32x2 %0, %1, %2, %3;" : "=l"(uh) : "l"(k0.v), "l"(S0.v), "l"(Ghi.v));
+    asm("add.rp.f32x2 %0, %1, %2;" : "=l"(tl) : "l"(ul), "l"(M.v));
+    asm("add.rp.f32x2 %0, %1, %2;" : "=l"(th) : "l"(uh), "l"(M.v));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(tlo_a), "=r"(tlo_b) : "l"(tl));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(thi_a), "=r"(thi_b) : "l"(th));
+}
+
 // ------------------------------------------------------------------ weights
 
 template <int WT>
@@ -203,12 +235,12 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 
 __device__ __forceinline__ void red_shared_add(uint32_t addr, int32_t v)
 {
-    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
 __device__ __forceinline__ void red_shared_add_u32(uint32_t addr, uint32_t v)
 {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
 __device__ __forceinline__ int4 lds128(uint32_t addr)

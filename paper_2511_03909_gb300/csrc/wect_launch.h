@@ -17,11 +17,10 @@ struct CubicalFwdArgs {
     int d, T;
     const double *range;          // [3] = lo, hi, step (resolved on the device)
     const double *beta;           // [T]
-    int Dt, R;                    // direction-tile width, rows per shared-memory tile
-    int CP;                       // pitch (words) of the octant-contribution planes
-    int wt;                       // weight storage type
-    int kflush;                   // vertices per histogram flush
-    int frac_bits;
+    int Dt;                       // direction-tile width (columns of the shared histogram)
+    int CP;                       // pitch (words) of the octant-contribution planes of a row
+    const int *perm;              // column -> direction (directions grouped by octant)
+    int kflush;                   // max vertices of one item (int32 histogram bound)
     int64_t climit;               // largest |c_o(v)| the accumulator mode supports
     int direct;                   // items cover whole complexes: scan in the CTA and store W
     unsigned long long *out;      // int64 difference tables (or W when direct) [count][d][T]
@@ -61,13 +60,13 @@ struct SimplexFwdArgs {
 // cubical
 cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem);   // dynamic smem attribute, outside capture
-size_t cubical_fwd_smem(int n, int nsplit, int T, int Dt, int R, int maxL0);
-int cubical_fwd_pitch(int n, int R, int maxL0);
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0);
+int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
-cudaError_t launch_cubical_bwd(int n, int wt, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
+cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
 size_t cubical_bwd_rsum_smem(int d, int R);
-cudaError_t launch_cubical_ecf(int n, int wt, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
-                               int frac_bits, unsigned long long *out, int64_t nv, cudaStream_t st);
+cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
+                               unsigned long long *out, int64_t nv, cudaStream_t st);
 cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
                                uint16_t *bins, cudaStream_t st);
 cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
@@ -99,6 +98,8 @@ cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, in
                                cudaStream_t st);
 cudaError_t launch_weights_to_fixed(int wt, const void *w, int64_t nv, int frac_bits, int64_t *out,
                                     unsigned long long *maxabs, int *bad, cudaStream_t st);
+cudaError_t launch_weights_to_w32(int wt, const void *w, int64_t nv, int frac_bits, int64_t limit, int32_t *out,
+                                  int *status, cudaStream_t st);
 cudaError_t launch_weights_check(int wt, const void *w, int64_t nv, int frac_bits, int64_t limit, int *status,
                                  cudaStream_t st);
 cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits,
