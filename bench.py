@@ -55,7 +55,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 100 ms while the timed region (and the soak before it) runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,7 +70,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -107,7 +107,8 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "nvidia-smi every 100 ms over >= 1.5 s of identical steps ending with the timed region"}
 
 
 # ------------------------------------------------------------------ oracle baseline
@@ -233,9 +234,17 @@ def run_gpu(args):
         step()
     barrier()
 
-    # ---- device-resident timed region
+    # ---- clock window: nvidia-smi samples every 100 ms cannot resolve a timed region of a few
+    # milliseconds, so the sampler runs over a soak of identical steps (>= 1.5 s) that ends
+    # with the timed region.
     clocks = ClockSampler(local)
     clocks.start()
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 1.5:
+        for _ in range(50):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     P.profile_enable(True)
     l0 = P.launch_count()
