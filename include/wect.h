@@ -228,6 +228,31 @@ WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d
 
 WECT_API void wect_batch_destroy(wect_batch b);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/*
+ * The paper has no counterpart to this entry point.  It serves callers that cannot allocate
+ * device memory: code that runs while a CUDA graph is being captured for later replay, hosts
+ * whose allocator or runtime owns every device byte, and services that must not allocate after
+ * start-up.  It computes exactly what wect_compute computes for the full cubical complex of a
+ * grid, with the same kernels, but allocates nothing: its scratch (threshold table, direction
+ * grouping, work queue, int32 copy of the weights) lives in one static device array of about
+ * 8.1 MB that every GPU loading this library holds until the process exits.
+ *   n, dims (host)   grid rank 1..3 and axis lengths (axis 0 fastest); at most 2^21 vertices
+ *   vertex_weights   (dev) uint8 [prod dims] for WECT_W_U8; ignored for WECT_W_ONE (other types:
+ *                    WECT_ERR_UNSUPPORTED)
+ *   dirs (dev)       [d][n] float64, 1 <= d <= 4096;  2 <= T <= 4096;  lo, hi as wect_compute
+ *   out (dev)        [d][T] int64, caller-allocated
+ * Sizes beyond these limits return WECT_ERR_INVALID_ARG (nothing is launched; the message is in
+ * wect_last_error).  The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress) and caches it: make that first call before any stream capture.
+ * Every call shares the one array and clears on its stream what must start at zero, so calls
+ * whose work overlaps on the GPU (other streams, or unordered host threads) race; order them.
+ */
+WECT_API wect_status wect_cubical_compute_static(int n, const int64_t *dims, const void *vertex_weights,
+                                                 wect_wtype wtype, const double *dirs, int d, int T, double lo,
+                                                 double hi, int64_t *out, wect_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Thread-local message for the last non-OK status on this thread ("" if none). */

@@ -91,6 +91,7 @@ def _declare(L):
         "wect_kernel_launch_count": (_i64, []),
         "wect_profile_enable": (_st, [_i]),
         "wect_profile_read": (_st, [_p, _p]),
+        "wect_cubical_compute_static": (_st, [_i, _p, _p, _i, _p, _i, _i, _d, _d, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -107,7 +108,7 @@ def exported_symbols():
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_autotune",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
-        "wect_profile_enable", "wect_profile_read",
+        "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static",
     ]
 
 
@@ -395,6 +396,29 @@ class WECTFunction(torch.autograd.Function):
         q, scale = grad_to_fixed(gW.contiguous(), ctx.T, gW.shape[1])
         grad = b.backward(ctx.dirs, ctx.T, ctx.lo, ctx.hi, q.contiguous(), scale)
         return None, grad, None, None, None, None
+
+
+# ------------------------------------------------------------------ allocation-free variant
+
+
+def cubical_wect_static(weights: torch.Tensor | None, dirs: torch.Tensor, T: int, lo: float = math.nan,
+                        hi: float = math.nan, out: torch.Tensor | None = None, dims=None) -> torch.Tensor:
+    """wect_cubical_compute_static: the WECT of a uint8 (or unweighted) grid without any device
+    allocation by the library (scratch in a static device array; see include/wect.h).  ``out``
+    may be preallocated by the caller."""
+    if weights is not None:
+        _require_cuda(weights, "weights", torch.uint8)
+        dims = list(reversed(weights.shape))
+    _require_cuda(dirs, "dirs", torch.float64)
+    n = len(dims)
+    d = dirs.shape[0]
+    if out is None:
+        out = torch.empty((d, T), dtype=torch.int64, device=dirs.device)
+    _require_cuda(out, "out", torch.int64)
+    dims_a = (C.c_int64 * n)(*[int(x) for x in dims])
+    _check(load().wect_cubical_compute_static(n, dims_a, _ptr(weights), W_U8 if weights is not None else W_ONE,
+                                              _ptr(dirs), d, T, lo, hi, _ptr(out), _stream()))
+    return out
 
 
 # ------------------------------------------------------------------ one-shot helpers

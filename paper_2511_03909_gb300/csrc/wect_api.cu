@@ -34,6 +34,11 @@ static wect_status fail(wect_status st, const char *fmt, ...)
     return st;
 }
 
+namespace wect {
+void note_error(const char *msg) { g_last_error = msg; }
+void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace wect
+
 static wect_status cuda_fail(cudaError_t e, const char *where)
 {
     if (e == cudaErrorMemoryAllocation)

@@ -107,4 +107,8 @@ cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offse
 cudaError_t launch_finite_check(const double *x, int64_t n, int *bad, int flag, cudaStream_t st);
 cudaError_t launch_index_check(const int32_t *idx, int64_t n, int64_t nv, int *bad, cudaStream_t st);
 
+// host-side bookkeeping shared with the C entry points (last error message, launch counter)
+void note_error(const char *msg);
+void note_launches(int64_t n);
+
 }  // namespace wect
