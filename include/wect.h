@@ -222,6 +222,17 @@ WECT_API wect_status wect_batch_compute_loop(wect_batch b, const double *dirs, i
 WECT_API wect_status wect_batch_backward(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                 const int64_t *dW, double scale, float *grad_w, wect_stream stream);
 
+/*
+ * Adjoint of wect_batch_compute for a float64 upstream gradient G = dL/dW (dev [count][d][T])
+ * with W in real units (the fixed-point table times 2^-frac_bits), so grad_w[v] = dL/dw_v for
+ * the real-valued vertex weights.  G is quantised on the device to int64 with the largest
+ * power-of-two scale 2^k that keeps d * T * max|G| * 2^k below 2^62 (exact when G's values are
+ * multiples of 2^-k, as for the gradient of a squared error between fixed-point transforms);
+ * the rest is wect_batch_backward.  Asynchronous: no host synchronisation.
+ */
+WECT_API wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                             const double *G, float *grad_w, wect_stream stream);
+
 /* Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest. */
 WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                 int64_t *scratch_out, wect_stream stream);

@@ -84,6 +84,7 @@ def _declare(L):
         "wect_batch_compute": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
         "wect_batch_compute_loop": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
         "wect_batch_backward": (_st, [_p, _p, _i, _i, _d, _d, _p, _d, _p, _p]),
+        "wect_batch_backward_f64": (_st, [_p, _p, _i, _i, _d, _d, _p, _p, _p]),
         "wect_batch_autotune": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
         "wect_batch_destroy": (None, [_p]),
         "wect_last_error": (C.c_char_p, []),
@@ -106,7 +107,8 @@ def exported_symbols():
         "wect_complex_num_vertices", "wect_complex_cell_counts", "wect_complex_device_status",
         "wect_complex_destroy", "wect_compute", "ecf_compute", "wect_backward", "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
-        "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_autotune",
+        "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
+        "wect_batch_autotune",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
         "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static",
     ]
@@ -342,6 +344,16 @@ class CubicalBatch:
         _check(fn(self._h, _ptr(dirs), d, T, lo, hi, _ptr(out), _stream()))
         return out
 
+    def backward_f64(self, dirs: torch.Tensor, T: int, lo: float, hi: float, G: torch.Tensor,
+                     grad: torch.Tensor | None = None) -> torch.Tensor:
+        """Adjoint for a float64 upstream gradient in real units (wect_batch_backward_f64)."""
+        _require_cuda(G, "G", torch.float64)
+        if grad is None:
+            grad = torch.empty(self.total, dtype=torch.float32, device=dirs.device)
+        _check(load().wect_batch_backward_f64(self._h, _ptr(dirs), dirs.shape[0], T, lo, hi, _ptr(G), _ptr(grad),
+                                              _stream()))
+        return grad
+
     def autotune(self, dirs: torch.Tensor, T: int, lo: float, hi: float):
         scratch = torch.empty((self.count, dirs.shape[0], T), dtype=torch.int64, device=dirs.device)
         _check(load().wect_batch_autotune(self._h, _ptr(dirs), dirs.shape[0], T, lo, hi, _ptr(scratch), _stream()))
@@ -379,8 +391,8 @@ class WECTFunction(torch.autograd.Function):
     """W = WECT(weights) for a CubicalBatch, with the library's exact adjoint as backward.
 
     forward(batch, weights_flat_f32, dirs, T, lo, hi) -> float64 [count][d][T] in real units
-    (int64 fixed-point result * 2^-frac_bits).  The upstream gradient is quantised to int64
-    fixed point (grad_to_fixed) and passed to wect_batch_backward.
+    (int64 fixed-point result * 2^-frac_bits).  backward passes the float64 upstream gradient to
+    wect_batch_backward_f64 (quantised to int64 fixed point on the device, no host sync).
     """
 
     @staticmethod
@@ -393,8 +405,7 @@ class WECTFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gW: torch.Tensor):
         b = ctx.batch
-        q, scale = grad_to_fixed(gW.contiguous(), ctx.T, gW.shape[1])
-        grad = b.backward(ctx.dirs, ctx.T, ctx.lo, ctx.hi, q.contiguous(), scale)
+        grad = b.backward_f64(ctx.dirs, ctx.T, ctx.lo, ctx.hi, gW.to(torch.float64).contiguous())
         return None, grad, None, None, None, None
 
 

@@ -168,6 +168,8 @@ struct Workspace {
     DBuf<int64_t> S;              // suffix sums of the upstream gradient
     DBuf<int64_t> Rv;             // per-vertex octant sums (adjoint)
     DBuf<unsigned long long> Iacc;
+    DBuf<long long> Gq;           // quantised upstream gradient
+    DBuf<double> gscale;          // its power-of-two scale
     DBuf<WorkItem> items;
     DBuf<WorkItem> items_bwd;
     // cache key of the uploaded item list
@@ -177,7 +179,8 @@ struct Workspace {
     void release()
     {
         range.release(); beta.release(); M.release(); counter.release(); perm.release(); octb.release();
-        bins.release(); S.release(); Rv.release(); Iacc.release(); items.release(); items_bwd.release();
+        bins.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
+        items_bwd.release();
     }
 };
 
@@ -855,7 +858,7 @@ extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, 
 static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const std::vector<GridDesc> &h_grids, int n,
                                     int wt, int frac_bits, int64_t total_nv, Workspace &ws, const double *dirs, int d,
                                     int T, double lo, double hi, const int64_t *dW, double scale, float *grad,
-                                    int *status, cudaStream_t st)
+                                    int *status, cudaStream_t st, const double *scale_dev = nullptr)
 {
     if (range_is_default(lo, hi) && n_grids != 1) return fail(WECT_ERR_UNSUPPORTED, "default range in a batch");
     wect_status s = ensure_common_ws(ws, T, d);
@@ -865,15 +868,18 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     CK(ws.Rv.ensure((size_t)total_nv * noct), "alloc Rv");
     CK(ws.perm.ensure((size_t)d), "alloc perm");
     CK(ws.octb.ensure(9), "alloc octb");
-    const int R = 8;
-    const size_t sm = cubical_bwd_rsum_smem(d, R);
-    if (sm > std::min<size_t>(smem_optin(), 200 * 1024)) return fail(WECT_ERR_UNSUPPORTED, "d too large for the adjoint");
+    // rows per filter tile: as many as fit next to the shared suffix table (up to 32)
+    int R = 32;
+    while (R > 1 && cubical_bwd_rsum_smem(d, T, R) > smem_optin() - 1024) R /= 2;
+    const size_t sm = cubical_bwd_rsum_smem(d, T, R);
+    if (sm > smem_optin() - 1024) return fail(WECT_ERR_UNSUPPORTED, "d x T too large for the adjoint's shared table");
     auto key = std::make_tuple(d, R);
     if (ws.items_bwd_key != key) {
         std::vector<WorkItem> items;
         for (int c = 0; c < n_grids; ++c) {
             const int rows = h_grids[c].rows;
-            const int per = std::max(R, ((std::max(1, 4096 / std::max(1, h_grids[c].L[0])) + R - 1) / R) * R);
+            // about 64K vertices per item: the shared suffix table is staged once per item
+            const int per = std::max(R, ((std::max(1, 65536 / std::max(1, h_grids[c].L[0])) + R - 1) / R) * R);
             for (int r0 = 0; r0 < rows; r0 += per) items.push_back(WorkItem{c, 0, r0, std::min(rows, r0 + per)});
         }
         CK(ws.items_bwd.ensure(items.size()), "alloc");
@@ -906,6 +912,7 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     a.Rv = ws.Rv.p;
     a.grad = grad;
     a.scale = scale;
+    a.scale_dev = scale_dev;
     a.frac_bits = frac_bits;
     a.total_nv = total_nv;
     {
@@ -1258,6 +1265,36 @@ extern "C" wect_status wect_batch_backward(wect_batch b, const double *dirs, int
     std::lock_guard<std::mutex> lk(b->mu);
     return cubical_backward(b->d_grids, b->count, b->h_grids, b->n, b->wtype, b->frac_bits, b->total_nv, b->ws, dirs, d, T,
                             lo, hi, dW, scale, grad_w, b->d_status, st);
+}
+
+static int ceil_log2(int64_t x)
+{
+    int k = 0;
+    while (((int64_t)1 << k) < x) ++k;
+    return k;
+}
+
+extern "C" wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
+                                               const double *G, float *grad_w, wect_stream stream)
+{
+    if (!b) return fail(WECT_ERR_INVALID_ARG, "NULL batch");
+    if (!dirs || !G || !grad_w) return fail(WECT_ERR_INVALID_ARG, "NULL pointer argument");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (range_is_default(lo, hi)) return fail(WECT_ERR_UNSUPPORTED, "batches need an explicit threshold range");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(b->mu);
+    if ((s = ensure_common_ws(b->ws, T, d))) return s;
+    const int64_t n = (int64_t)b->count * d * T;
+    CK(b->ws.Gq.ensure((size_t)n), "alloc");
+    CK(b->ws.gscale.ensure(1), "alloc");
+    KL(launch_grad_quantize(G, n, ceil_log2(T) + ceil_log2(d), b->ws.M.p, b->ws.Gq.p, b->ws.gscale.p, b->d_status, st),
+       "grad_quantize");
+    g_launches++;
+    return cubical_backward(b->d_grids, b->count, b->h_grids, b->n, b->wtype, b->frac_bits, b->total_nv, b->ws, dirs, d, T,
+                            lo, hi, reinterpret_cast<const int64_t *>(b->ws.Gq.p), 1.0, grad_w, b->d_status, st,
+                            b->ws.gscale.p);
 }
 
 extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,

@@ -185,6 +185,33 @@ __global__ void max_abs_f64_kernel(const double *x, int64_t n, int stride, int o
     if ((threadIdx.x & 31) == 0) atomicMax(Mbits, m);
 }
 
+// Upstream float64 gradient -> int64 table with the largest power-of-two scale 2^k that keeps
+// hr * max|G| * 2^k < 2^62 (hr = headroom, d * T rounded up to a power of two), so the adjoint's
+// int64 sums over thresholds and directions cannot overflow.  out = rint(G * 2^k) (ties to
+// even), *scale = 2^-k.  Non-finite G flags the status word.
+__global__ void grad_quantize_kernel(const double *G, int64_t n, const unsigned long long *maxbits, int log2_headroom,
+                                     long long *out, double *scale, int *status)
+{
+    const double m = __longlong_as_double((long long)*maxbits);
+    int k = 0;
+    if (m > 0.0 && isfinite(m)) {
+        int e;
+        frexp(m, &e);                                      // m < 2^e
+        k = 62 - log2_headroom - e;
+        k = max(min(k, 1000), -1000);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = ldexp(1.0, -k);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = G[i];
+        if (!isfinite(x)) {
+            atomicOr(status, kStatusBadIndex);
+            out[i] = 0;
+            continue;
+        }
+        out[i] = (m > 0.0) ? __double2ll_rn(ldexp(x, k)) : 0ll;
+    }
+}
+
 __global__ void finite_check_kernel(const double *x, int64_t n, int *bad, int flag)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -280,6 +307,20 @@ cudaError_t launch_weights_to_w32(int wt, const void *w, int64_t nv, int frac_bi
     case WT_F32: weights_to_w32_kernel<WT_F32><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
     default: weights_to_w32_kernel<WT_ONE><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_quantize(const double *G, int64_t n, int log2_headroom, unsigned long long *maxbits,
+                                 long long *out, double *scale, int *status, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        max_abs_f64_kernel<<<grid_for(n, 256), 256, 0, st>>>(G, n, 1, 0, maxbits);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    grad_quantize_kernel<<<grid_for(std::max<int64_t>(n, 1), 256), 256, 0, st>>>(G, n, maxbits, log2_headroom, out, scale,
+                                                                               status);
     return cudaGetLastError();
 }
 

@@ -423,81 +423,114 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 
 // ------------------------------------------------------------------ backward
 
-// Per-vertex octant sums of the suffix-scanned upstream gradient:
-//     Rv[v][o] = sum over directions p of octant o of S[p][bin_p(v)].
-// Lanes <-> vertices of a row; the direction loop is uniform across the warp and visits the
-// directions octant by octant (perm / octant bounds from the setup kernel).
+// Per-vertex octant sums of the suffix-scanned upstream gradient,
+//     Rv[o][v] = sum over directions p of octant o of S[p][bin_p(v)]   (octant-major planes),
+// for one item (complex, row range).  Lanes <-> vertices of a row; the direction loop is
+// uniform across the warp and visits the directions octant by octant.  The suffix table of the
+// complex sits in shared memory in octant order ([d][T] int64), the per-(row, direction)
+// filter constants in a [R][d] float4 table (broadcast loads).  Undecided bins are fixed after
+// each group of 8 directions with the exact float64 height.
 template <int N>
-__global__ void __launch_bounds__(256) cubical_bwd_rsum_kernel(const CubicalBwdArgs P)
+__global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const CubicalBwdArgs P)
 {
     constexpr int NOCT = 1 << N;
+    constexpr int G = 4;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int T = P.T, d = P.d;
+    const int T = P.T, d = P.d, RB = P.R;
     const WorkItem W = P.items[blockIdx.x];
     const GridDesc g = P.grids[W.cx];
     const int L0 = g.L[0], L1 = g.L[1];
-    // shared: row filters [rows_per_block][d] (Glo, Ghi, nr) + S0 [d]
-    const int RB = P.R;
-    float *sGlo = reinterpret_cast<float *>(smem);
-    float *sGhi = sGlo + RB * d;
-    int *sNr = reinterpret_cast<int *>(sGhi + RB * d);
-    float *sS0 = reinterpret_cast<float *>(sNr + RB * d);
+    long long *Ss = reinterpret_cast<long long *>(smem);                 // [d][T], octant order
+    DirFilter *dfil = reinterpret_cast<DirFilter *>(Ss + (size_t)d * T);  // [d]
+    float4 *rowf = reinterpret_cast<float4 *>(                             // [RB][d]
+        smem + (((size_t)d * T * 8 + (size_t)d * sizeof(DirFilter) + 15) & ~(size_t)15));
+    __shared__ int octb[9];
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
-    const int64_t *S = P.S + (int64_t)W.cx * d * T;
-    const int segs = (L0 + 31) >> 5;
-    const int nwarps = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long *S = reinterpret_cast<const long long *>(P.S) + (int64_t)W.cx * d * T;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
 
+    if (tid <= NOCT) octb[tid] = P.octb[tid];
+    for (int idx = tid; idx < d * T; idx += blockDim.x) {
+        const int k = idx / T, q = idx - k * T;
+        Ss[idx] = S[(int64_t)P.perm[k] * T + q];
+    }
+    for (int k = tid; k < d; k += blockDim.x) {
+        const int p = P.perm[k];
+        double sv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int a = 0; a < N; ++a) sv[a] = P.dirs[(int64_t)p * N + a];
+        dfil[k] = make_dir_filter<N>(sv, g.L, lo, hi, step, T);
+    }
+    const int segs = (L0 + 31) >> 5;
     for (int rt = W.r0; rt < W.r1; rt += RB) {
         const int nrt = min(RB, W.r1 - rt);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < nrt * d; idx += blockDim.x) {
+        for (int idx = tid; idx < nrt * d; idx += blockDim.x) {
             const int rl = idx / d, k = idx - rl * d;
-            const int p = P.perm[k];
-            double s[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int a = 0; a < N; ++a) s[a] = P.dirs[(int64_t)p * N + a];
-            const DirFilter F = make_dir_filter<N>(s, g.L, lo, hi, step, T);
             const int r = rt + rl;
-            const RowFilter rf = make_row_filter<N>(F, r % L1, r / L1, g.L);
-            sGlo[rl * d + k] = rf.Glo;
-            sGhi[rl * d + k] = rf.Ghi;
-            sNr[rl * d + k] = rf.nr;
-            if (rl == 0) sS0[k] = F.S0;
+            const DirFilter f = dfil[k];
+            const RowFilter rf = make_row_filter<N>(f, r % L1, r / L1, g.L);
+            rowf[rl * d + k] = make_float4(rf.Glo, rf.Ghi, f.S0, __int_as_float(rf.nr - kMagicBits));
         }
         __syncthreads();
         for (int job = wid; job < nrt * segs; job += nwarps) {
             const int rl = job / segs, seg = job - rl * segs;
-            const int i0 = seg * 32 + lane;
-            const bool live = i0 < L0;
+            const int i0 = min(seg * 32 + lane, L0 - 1);
+            const bool live = seg * 32 + lane < L0;
             const int r = rt + rl, i1 = r % L1, i2 = r / L1;
             const float kk = (float)(2 * i0 - (L0 - 1));
-            int64_t acc[NOCT];
-#pragma unroll
+            const float4 *rf = rowf + rl * d;
+            const int64_t vout = g.v_off + (int64_t)i0 + (int64_t)L0 * r;
+#pragma unroll 1
             for (int o = 0; o < NOCT; ++o) {
-                int64_t a = 0;
-                const int kb = P.octb[o], ke = P.octb[o + 1];
-                for (int k = kb; k < ke; ++k) {
-                    const float S0 = sS0[k];
-                    const float Glo = sGlo[rl * d + k], Ghi = sGhi[rl * d + k];
-                    const int nr = sNr[rl * d + k];
+                long long a = 0;
+                const int kb = octb[o], ke = octb[o + 1];
+                int k0 = kb;
+                // full groups of G directions: filter loads first, then bins and gathers
+                for (; k0 + G <= ke; k0 += G) {
+                    float4 f[G];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) f[u] = rf[k0 + u];
+                    int bt[G];
+                    int bad = 0;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        int tlo, thi;
+                        filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
+                        bad |= tlo ^ thi;
+                        bt[u] = min(max(thi + __float_as_int(f[u].w), 0), T - 1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < G; ++u) a += Ss[(k0 + u) * T + bt[u]];
+                    if (__any_sync(0xffffffffu, bad != 0)) {
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            int tlo, thi;
+                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
+                            if (tlo != thi) {
+                                const int k = k0 + u;
+                                const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]),
+                                                            grid_coord(i2, g.L[2]), P.dirs + (int64_t)P.perm[k] * N);
+                                const int be = exact_bin_from(h, P.beta, T, bt[u]);
+                                a += Ss[k * T + be] - Ss[k * T + bt[u]];
+                            }
+                        }
+                    }
+                }
+                // remainder, one direction at a time
+                for (; k0 < ke; ++k0) {
+                    const float4 f = rf[k0];
                     int tlo, thi;
-                    filter_ceil(kk, S0, Glo, Ghi, tlo, thi);
-                    int b = thi - kMagicBits + nr;
-                    if (tlo != thi && live) {
-                        const int p = P.perm[k];
-                        const double *sp = P.dirs + (int64_t)p * N;
-                        const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]), sp);
+                    filter_ceil(kk, f.z, f.x, f.y, tlo, thi);
+                    int b = min(max(thi + __float_as_int(f.w), 0), T - 1);
+                    if (tlo != thi) {
+                        const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]),
+                                                    P.dirs + (int64_t)P.perm[k0] * N);
                         b = exact_bin_from(h, P.beta, T, b);
                     }
-                    b = min(max(b, 0), T - 1);
-                    if (live) a += __ldg(S + (int64_t)P.perm[k] * T + b);
+                    a += Ss[k0 * T + b];
                 }
-                acc[o] = a;
-            }
-            if (live) {
-                const int64_t v = (int64_t)i0 + (int64_t)L0 * r;
-#pragma unroll
-                for (int o = 0; o < NOCT; ++o) P.Rv[(g.v_off + v) * NOCT + o] = acc[o];
+                if (live) P.Rv[(int64_t)o * P.total_nv + vout] = a;
             }
         }
     }
@@ -505,14 +538,16 @@ __global__ void __launch_bounds__(256) cubical_bwd_rsum_kernel(const CubicalBwdA
 
 // Route each cell's gradient to its heaviest vertex and sum exactly (128-bit):
 //     I_v = sum over cells s containing v whose heaviest vertex is v (ties -> lowest index) of
-//           (-1)^dim(s) sum_o Rv[corner_o(s)][o].
+//           (-1)^dim(s) sum_o Rv[o][corner_o(s)].
+// The neighbours that beat v (heavier, or as heavy with a lower index) form a bit mask over the
+// 3^n neighbourhood; v is the heaviest vertex of a cell iff the mask misses every cell vertex.
 template <int N>
 __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwdArgs P)
 {
     constexpr int NOCT = 1 << N;
     constexpr int NB = (N == 1) ? 3 : (N == 2) ? 9 : 27;
+    constexpr int CENTER = (NB - 1) / 2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // locate the complex by binary search on v_off
     if (gid >= P.total_nv) return;
     int lo_c = 0, hi_c = P.n_grids - 1;
     while (lo_c < hi_c) {
@@ -523,67 +558,71 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
     const int64_t v = gid - g.v_off;
     const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
     const int i0 = (int)(v % L0), i1 = (int)((v / L0) % L1), i2 = (int)(v / ((int64_t)L0 * L1));
-    int64_t w[NB];
-    bool ok[NB];
+    const int32_t *wp = g.w + v;
+    const int32_t wv = __ldg(wp);
+    // neighbour offsets (flat, int32), in-bounds mask and "beats v" mask over the 3^n neighbourhood
+    int off[NB];
+    uint32_t okm = 0, beat = 0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
         const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
-        const int j0 = i0 + dx, j1 = i1 + dy, j2 = i2 + dz;
-        ok[t] = j0 >= 0 && j0 < L0 && j1 >= 0 && j1 < L1 && j2 >= 0 && j2 < L2;
-        w[t] = ok[t] ? (int64_t)__ldg(g.w + v + dx + (int64_t)L0 * (dy + (int64_t)L1 * dz)) : 0;
-    }
-    const int center = (N == 1) ? 1 : (N == 2) ? 4 : 13;
-    const int64_t wv = w[center];
-    int64_t Ihi = 0;
-    uint64_t Ilo = 0;
-    // each neighbour offset t defines the cell spanning v and v + delta(t)
-#pragma unroll
-    for (int t = 0; t < NB; ++t) {
-        if (!ok[t]) continue;
-        const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
-        const int dlt[3] = {dx, dy, dz};
-        // is v the heaviest vertex of the cell (ties to the lowest index)?
-        bool arg = true;
-#pragma unroll
-        for (int u = 0; u < NB; ++u) {
-            const int ux = u % 3 - 1, uy = (N >= 2) ? (u / 3) % 3 - 1 : 0, uz = (N >= 3) ? u / 9 - 1 : 0;
-            const int ud[3] = {ux, uy, uz};
-            bool inside = (u != center);
-#pragma unroll
-            for (int a = 0; a < N; ++a) inside = inside && (ud[a] == 0 || ud[a] == dlt[a]);
-            if (inside) {
-                // vertex u of the cell: offset ud; its flat index is below v iff the offset is lexicographically negative
-                const int64_t off = ux + (int64_t)L0 * (uy + (int64_t)L1 * uz);
-                if (w[u] > wv || (w[u] == wv && off < 0)) arg = false;
+        off[t] = dx + L0 * (dy + L1 * dz);
+        const bool ok = i0 + dx >= 0 && i0 + dx < L0 && i1 + dy >= 0 && i1 + dy < L1 && i2 + dz >= 0 && i2 + dz < L2;
+        if (ok) {
+            okm |= 1u << t;
+            if (t != CENTER) {
+                const int32_t wu = __ldg(wp + off[t]);
+                // u's flat index is below v's iff its offset is lexicographically negative
+                const bool below = (dz < 0) || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
+                if (wu > wv || (wu == wv && below)) beat |= 1u << t;
             }
         }
-        if (!arg) continue;
-        // g(cell) = sum_o Rv[sign corner under octant o][o]
-        int64_t gs = 0;
+    }
+    const long long *Rp[NOCT];
 #pragma unroll
-        for (int o = 0; o < NOCT; ++o) {
-            int cofs[3] = {0, 0, 0};
+    for (int o = 0; o < NOCT; ++o) Rp[o] = reinterpret_cast<const long long *>(P.Rv) + (int64_t)o * P.total_nv + gid;
+    int64_t Ihi = 0;
+    uint64_t Ilo = 0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const int dlt[3] = {t % 3 - 1, (N >= 2) ? (t / 3) % 3 - 1 : 0, (N >= 3) ? t / 9 - 1 : 0};
+        // vertex mask of the cell spanning v and v + dlt (compile-time)
+        uint32_t cm = 0;
+#pragma unroll
+        for (int sm = 0; sm < NOCT; ++sm) {
+            int f[3] = {0, 0, 0};
+            bool ok = true;
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                if (dlt[a] != 0) {
-                    const bool up = (o >> a) & 1;
-                    // corner coordinate: upper end if up, lower end otherwise
-                    cofs[a] = up ? max(dlt[a], 0) : min(dlt[a], 0);
+                if ((sm >> a) & 1) {
+                    if (dlt[a] == 0) ok = false;
+                    f[a] = dlt[a];
                 }
             }
-            const int64_t cv = v + cofs[0] + (int64_t)L0 * (cofs[1] + (int64_t)L1 * cofs[2]);
-            gs += P.Rv[(g.v_off + cv) * NOCT + o];
+            if (ok) cm |= 1u << ((f[0] + 1) + (N >= 2 ? 3 * (f[1] + 1) : 0) + (N >= 3 ? 9 * (f[2] + 1) : 0));
+        }
+        if ((okm & (1u << t)) == 0 || (beat & cm) != 0) continue;
+        // g(cell) = sum_o Rv[o][sign corner under octant o]
+        long long gs = 0;
+#pragma unroll
+        for (int o = 0; o < NOCT; ++o) {
+            int c[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+                if (dlt[a] != 0) c[a] = ((o >> a) & 1) ? max(dlt[a], 0) : min(dlt[a], 0);
+            const int ci = (c[0] + 1) + (N >= 2 ? 3 * (c[1] + 1) : 0) + (N >= 3 ? 9 * (c[2] + 1) : 0);
+            gs += __ldg(Rp[o] + off[ci]);
         }
         int dimc = 0;
 #pragma unroll
         for (int a = 0; a < N; ++a) dimc += (dlt[a] != 0);
         if (dimc & 1) gs = -gs;
-        // 128-bit accumulate
         const uint64_t old = Ilo;
         Ilo += (uint64_t)gs;
         Ihi += (gs < 0 ? -1 : 0) + (Ilo < old ? 1 : 0);
     }
-    P.grad[g.v_off + v] = (float)(i128_to_double(Ihi, Ilo) * P.scale);
+    const double scale = P.scale_dev ? *P.scale_dev : P.scale;
+    P.grad[gid] = (float)(i128_to_double(Ihi, Ilo) * scale);
 }
 
 // ------------------------------------------------------------------ ECF on a grid (one vertex filter)
@@ -730,7 +769,7 @@ cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size
         e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                  (int)smem_rsum);                                                              \
         if (e != cudaSuccess) return e;                                                                        \
-        cubical_bwd_rsum_kernel<NN><<<n_items, 256, smem_rsum, st>>>(a);                                       \
+        cubical_bwd_rsum_kernel<NN><<<n_items, 1024, smem_rsum, st>>>(a);                                      \
         if ((e = cudaGetLastError()) != cudaSuccess) return e;                                                 \
         cubical_bwd_route_kernel<NN><<<blocks, 256, 0, st>>>(a);                                               \
     } while (0)
@@ -741,7 +780,11 @@ cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size
     return cudaGetLastError();
 }
 
-size_t cubical_bwd_rsum_smem(int d, int R) { return (size_t)R * d * 12u + (size_t)d * 4u; }
+size_t cubical_bwd_rsum_smem(int d, int T, int R)
+{
+    const size_t a = (size_t)d * T * 8u + (size_t)d * sizeof(DirFilter);
+    return ((a + 15) & ~(size_t)15) + (size_t)R * d * sizeof(float4);
+}
 
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
                                unsigned long long *out, int64_t nv, cudaStream_t st)

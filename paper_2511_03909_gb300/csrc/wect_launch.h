@@ -38,9 +38,10 @@ struct CubicalBwdArgs {
     const int *octb;              // [2^n + 1] octant bounds in perm
     int R;
     const int64_t *S;             // suffix sums [count][d][T]
-    int64_t *Rv;                  // [total_nv][2^n]
+    int64_t *Rv;                  // [2^n][total_nv] (octant-major planes)
     float *grad;                  // [total_nv]
     double scale;
+    const double *scale_dev;      // when set, the scale is read from the device (quantised upstream)
     int frac_bits;
     int64_t total_nv;
 };
@@ -64,7 +65,7 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0);
 int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
 cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
-size_t cubical_bwd_rsum_smem(int d, int R);
+size_t cubical_bwd_rsum_smem(int d, int T, int R);
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
                                unsigned long long *out, int64_t nv, cudaStream_t st);
 cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
@@ -104,6 +105,8 @@ cudaError_t launch_weights_check(int wt, const void *w, int64_t nv, int frac_bit
                                  cudaStream_t st);
 cudaError_t launch_max_abs_f64(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits,
                                cudaStream_t st);
+cudaError_t launch_grad_quantize(const double *G, int64_t n, int log2_headroom, unsigned long long *maxbits,
+                                 long long *out, double *scale, int *status, cudaStream_t st);
 cudaError_t launch_finite_check(const double *x, int64_t n, int *bad, int flag, cudaStream_t st);
 cudaError_t launch_index_check(const int32_t *idx, int64_t n, int64_t nv, int *bad, cudaStream_t st);
 
