@@ -911,6 +911,8 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     a.S = ws.S.p;
     a.Rv = ws.Rv.p;
     a.grad = grad;
+    a.v_begin = 0;
+    a.v_end = total_nv;
     a.scale = scale;
     a.scale_dev = scale_dev;
     a.frac_bits = frac_bits;
@@ -918,8 +920,8 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     {
         ProfScope prof(st);
         KL(launch_cubical_bwd(n, a, ws.n_items_bwd, sm, st), "cubical_bwd");
+        g_launches++;   // rsum + route
     }
-    g_launches++;   // rsum + route
     return WECT_OK;
 }
 

@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
     const long long *S = reinterpret_cast<const long long *>(P.S) + (int64_t)W.cx * d * T;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *clampw = reinterpret_cast<uint32_t *>(rowf + (size_t)RB * d);    // [RB*d/32] bit per (row, direction)
 
     if (tid <= NOCT) octb[tid] = P.octb[tid];
     for (int idx = tid; idx < d * T; idx += blockDim.x) {
@@ -465,12 +466,20 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
     for (int rt = W.r0; rt < W.r1; rt += RB) {
         const int nrt = min(RB, W.r1 - rt);
         __syncthreads();
+        for (int i = tid; i < (RB * d + 31) / 32; i += blockDim.x) clampw[i] = 0;
+        __syncthreads();
         for (int idx = tid; idx < nrt * d; idx += blockDim.x) {
             const int rl = idx / d, k = idx - rl * d;
             const int r = rt + rl;
             const DirFilter f = dfil[k];
             const RowFilter rf = make_row_filter<N>(f, r % L1, r / L1, g.L);
+            // bins of the whole row provably inside [0, T-1]?  (as in the forward kernel)
+            const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
+            const float lowf = __fadd_rd(__fsub_rd(rf.Glo, A), (float)(rf.nr - 1));
+            const float highf = __fadd_ru(__fadd_ru(rf.Ghi, A), (float)(rf.nr + 1));
+            const bool inr = (lowf >= 0.0f) && (highf <= (float)(T - 1));
             rowf[rl * d + k] = make_float4(rf.Glo, rf.Ghi, f.S0, __int_as_float(rf.nr - kMagicBits));
+            if (!inr) atomicOr(&clampw[(rl * d + k) >> 5], 1u << ((rl * d + k) & 31));
         }
         __syncthreads();
         for (int job = wid; job < nrt * segs; job += nwarps) {
@@ -491,14 +500,29 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
                     float4 f[G];
 #pragma unroll
                     for (int u = 0; u < G; ++u) f[u] = rf[k0 + u];
+                    // any direction of the group whose row may leave the threshold range?
+                    const int bit = rl * d + k0;
+                    const uint32_t cw = ((clampw[bit >> 5] >> (bit & 31)) |
+                                         ((bit & 31) + G > 32 ? clampw[(bit >> 5) + 1] << (32 - (bit & 31)) : 0u)) &
+                                        ((1u << G) - 1u);
                     int bt[G];
                     int bad = 0;
+                    if (cw == 0) {
 #pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        int tlo, thi;
-                        filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
-                        bad |= tlo ^ thi;
-                        bt[u] = min(max(thi + __float_as_int(f[u].w), 0), T - 1);
+                        for (int u = 0; u < G; ++u) {
+                            int tlo, thi;
+                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
+                            bad |= tlo ^ thi;
+                            bt[u] = thi + __float_as_int(f[u].w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            int tlo, thi;
+                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
+                            bad |= tlo ^ thi;
+                            bt[u] = min(max(thi + __float_as_int(f[u].w), 0), T - 1);
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < G; ++u) a += Ss[(k0 + u) * T + bt[u]];
@@ -547,8 +571,8 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
     constexpr int NOCT = 1 << N;
     constexpr int NB = (N == 1) ? 3 : (N == 2) ? 9 : 27;
     constexpr int CENTER = (NB - 1) / 2;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= P.total_nv) return;
+    const int64_t gid = P.v_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= P.v_end) return;
     int lo_c = 0, hi_c = P.n_grids - 1;
     while (lo_c < hi_c) {
         const int mid = (lo_c + hi_c + 1) >> 1;
@@ -763,7 +787,8 @@ int cubical_fwd_threads() { return kFwdThreads; }
 cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
 {
     cudaError_t e;
-    const int blocks = (int)((a.total_nv + 255) / 256);
+    const int blocks = (int)((a.v_end - a.v_begin + 255) / 256);
+    if (n_items <= 0 || blocks <= 0) return cudaSuccess;
 #define BWD(NN)                                                                                                \
     do {                                                                                                       \
         e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
@@ -783,7 +808,7 @@ cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size
 size_t cubical_bwd_rsum_smem(int d, int T, int R)
 {
     const size_t a = (size_t)d * T * 8u + (size_t)d * sizeof(DirFilter);
-    return ((a + 15) & ~(size_t)15) + (size_t)R * d * sizeof(float4);
+    return ((a + 15) & ~(size_t)15) + (size_t)R * d * sizeof(float4) + (size_t)((R * d + 31) / 32 + 1) * 4u;
 }
 
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,

@@ -40,6 +40,7 @@ struct CubicalBwdArgs {
     const int64_t *S;             // suffix sums [count][d][T]
     int64_t *Rv;                  // [2^n][total_nv] (octant-major planes)
     float *grad;                  // [total_nv]
+    int64_t v_begin, v_end;       // vertex range the routing kernel covers
     double scale;
     const double *scale_dev;      // when set, the scale is read from the device (quantised upstream)
     int frac_bits;
