@@ -328,7 +328,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     int32_t *hist = reinterpret_cast<int32_t *>(smem);                          // NSPLIT planes [T][Dt]
     DirFilter *dirf = reinterpret_cast<DirFilter *>(hist + NSPLIT * histWords);  // [Dt]
     const int rowbuf = NSPLIT * NOCT * CP;                                       // words of one row buffer
-    int32_t *cgrp = reinterpret_cast<int32_t *>(dirf + Dt) + rgroup * 2 * rowbuf;  // this group's 2 buffers
+    const int nbuf = (WC == 1) ? 1 : 2;     // a one-warp group needs no second buffer (warp-synchronous)
+    int32_t *cgrp = reinterpret_cast<int32_t *>(dirf + Dt) + rgroup * nbuf * rowbuf;
     const uint32_t histAddr = smem_addr(hist);
     const uint32_t HOFF = (uint32_t)histWords * 4u;
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         // row of octant contributions (one group barrier per row, no block-wide barrier)
         int parity = 0;
         for (int r = W.r0 + rgroup; r < W.r1; r += RG, parity ^= 1) {
-            int32_t *crow = cgrp + parity * rowbuf;
+            int32_t *crow = cgrp + (nbuf == 2 ? parity : 0) * rowbuf;
+            if (nbuf == 1) __syncwarp();        // the previous row's reads are done before the rewrite
             const int i1 = r % L1, i2 = r / L1;
             for (int i0 = gtid; i0 < L0; i0 += gthreads) {
                 int32_t c[NOCT];
@@ -779,7 +781,8 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0)
     const int WC = Dt / (32 * dpl);
     const int RG = (kFwdThreads / 32) / WC;
     const size_t rowbuf = (size_t)nsplit * noct * cubical_fwd_pitch(maxL0);
-    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * 2 * rowbuf * 4u;
+    const int nbuf = (WC == 1) ? 1 : 2;
+    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u;
 }
 
 int cubical_fwd_threads() { return kFwdThreads; }
