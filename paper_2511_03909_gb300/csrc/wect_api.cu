@@ -165,6 +165,7 @@ struct Workspace {
     DBuf<int> counter;            // work-queue head
     DBuf<int> perm, octb;         // octant grouping of the directions
     DBuf<uint16_t> bins;          // vertex bins
+    DBuf<float> dtab;             // [d][8] float32 bin filter per direction (simplicial)
     DBuf<int64_t> S;              // suffix sums of the upstream gradient
     DBuf<int64_t> Rv;             // per-vertex octant sums (adjoint)
     DBuf<unsigned long long> Iacc;
@@ -179,7 +180,7 @@ struct Workspace {
     void release()
     {
         range.release(); beta.release(); M.release(); counter.release(); perm.release(); octb.release();
-        bins.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
+        bins.release(); dtab.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
         items_bwd.release();
     }
 };
@@ -201,6 +202,7 @@ struct wect_complex_s {
     int64_t cells[4] = {0, 0, 0, 0};
     // simplicial
     double *d_coords = nullptr;
+    float *d_xf = nullptr;         // float32 copies of the coordinates (round to nearest)
     int max_dim = 0;
     int64_t counts[4] = {0, 0, 0, 0};
     int32_t *d_simp[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -576,6 +578,10 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
         return cleanup(cuda_fail(e, "copy coords"));
     if ((e = launch_finite_check(c->d_coords, n_vertices * n, d_bad + 0, 1, st))) return cleanup(cuda_fail(e, "finite_check"));
     g_launches++;
+    if ((e = cudaMalloc((void **)&c->d_xf, (size_t)n_vertices * n * sizeof(float))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "alloc coords"));
+    if ((e = launch_coords_to_f32(c->d_coords, n_vertices * n, c->d_xf, st))) return cleanup(cuda_fail(e, "coords_to_f32"));
+    g_launches++;
     // per-axis max |x| into range[3..5]
     std::vector<unsigned long long> zeros(3, 0ull);
     unsigned long long *d_xm = reinterpret_cast<unsigned long long *>(c->ws.range.p + 3);
@@ -659,6 +665,7 @@ extern "C" void wect_complex_destroy(wect_complex c)
     cudaDeviceSynchronize();
     if (c->d_w32) cudaFree(c->d_w32);
     if (c->d_coords) cudaFree(c->d_coords);
+    if (c->d_xf) cudaFree(c->d_xf);
     for (int i = 0; i < 4; ++i) {
         if (c->d_simp[i]) cudaFree(c->d_simp[i]);
         if (c->d_sw[i]) cudaFree(c->d_sw[i]);
@@ -755,11 +762,13 @@ static wect_status simplicial_range(wect_complex c, const double *dirs, int d, i
     const bool dflt = range_is_default(lo, hi);
     if (dflt) {
         CK(cudaMemsetAsync(c->ws.M.p, 0, 2 * sizeof(unsigned long long), st), "memset");
-        KL(launch_simplicial_max_abs(c->n, c->d_coords, c->nv, dirs, d, c->ws.M.p,
+        KL(launch_simplicial_max_abs(c->n, c->d_coords, c->d_xf, c->nv, dirs, d, c->ws.M.p,
                                      reinterpret_cast<float *>(c->ws.M.p + 1), st), "max_abs");
         g_launches++;    // two passes
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
+    CK(c->ws.dtab.ensure((size_t)d * 8), "alloc filter table");
+    KL(launch_dir_filters(c->n, dirs, d, T, c->ws.range.p, c->ws.dtab.p, st), "dir_filters");
     return WECT_OK;
 }
 
@@ -778,7 +787,8 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
     const int grid = sm_count();
     ProfScope prof(st);
     for (int dt = 0; dt * Dt < d; ++dt) {
-        KL(launch_vertex_bins(c->n, c->d_coords, c->nv, dirs, d, dt, Dt, T, c->ws.range.p, c->ws.beta.p, c->ws.bins.p, st),
+        KL(launch_vertex_bins(c->n, c->d_coords, c->d_xf, c->nv, dirs, c->ws.dtab.p, d, dt, Dt, T, c->ws.beta.p, c->ws.bins.p,
+                              st),
            "vertex_bins");
         for (int i = 0; i <= c->max_dim; ++i) {
             if (c->counts[i] == 0) continue;
@@ -954,7 +964,7 @@ extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, 
     if ((s = simplicial_range(c, dirs, d, T, lo, hi, st))) return s;
     KL(launch_suffix_rows(dW, c->ws.S.p, d, T, INT64_MAX / d, c->d_status, st), "suffix_rows");
     const int32_t *simp[4] = {nullptr, c->d_simp[1], c->d_simp[2], c->d_simp[3]};
-    CK(launch_simplicial_bwd(c->n, c->d_coords, c->nv, simp, c->counts, c->max_dim, c->d_sw[0], dirs, d, T, c->ws.range.p,
+    CK(launch_simplicial_bwd(c->n, c->d_coords, c->d_xf, c->nv, simp, c->counts, c->max_dim, c->d_sw[0], dirs, d, T, c->ws.dtab.p,
                              c->ws.beta.p, c->ws.S.p, c->ws.bins.p, c->ws.Iacc.p, grad_w, scale, st),
        "simplicial_bwd");
     g_launches += 1 + ((d + 31) / 32) * (1 + c->max_dim + 1);

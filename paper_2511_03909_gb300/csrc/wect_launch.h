@@ -75,18 +75,22 @@ cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs
                                 cudaStream_t st);
 
 // simplicial
-cudaError_t launch_vertex_bins(int n, const double *coords, int64_t nv, const double *dirs, int d, int dtile, int Dt,
-                               int T, const double *range, const double *beta, uint16_t *bins, cudaStream_t st);
+cudaError_t launch_dir_filters(int n, const double *dirs, int d, int T, const double *range, float *tab,
+                               cudaStream_t st);
+cudaError_t launch_coords_to_f32(const double *x, int64_t n, float *xf, cudaStream_t st);
+cudaError_t launch_vertex_bins(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
+                               const float *tab, int d, int dtile, int Dt, int T, const double *beta, uint16_t *bins,
+                               cudaStream_t st);
 cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st);
 size_t simplex_fwd_smem(int nsplit, int T, int Dt);
-cudaError_t launch_simplicial_max_abs(int n, const double *coords, int64_t nv, const double *dirs, int d,
-                                      unsigned long long *Mbits, float *Lbits_scratch, cudaStream_t st);
+cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
+                                      int d, unsigned long long *Mbits, float *Lscratch, cudaStream_t st);
 cudaError_t launch_simplex_weights_max(const int32_t *simp, int64_t k, int m, const int64_t *vw, int64_t *sw,
                                        cudaStream_t st);
-cudaError_t launch_simplicial_bwd(int n, const double *coords, int64_t nv, const int32_t *const *simp,
+cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, int64_t nv, const int32_t *const *simp,
                                   const int64_t *counts, int max_dim, const int64_t *vw, const double *dirs, int d,
-                                  int T, const double *range, const double *beta, const int64_t *S,
-                                  uint16_t *bins_all, unsigned long long *Iacc, float *grad, double scale,
+                                  int T, const float *tab, const double *beta, const int64_t *S,
+                                  uint16_t *bins, unsigned long long *Iacc, float *grad, double scale,
                                   cudaStream_t st);
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
                                const uint16_t *bins, int T, unsigned long long *out, cudaStream_t st);
