@@ -880,8 +880,8 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     CK(ws.octb.ensure(9), "alloc octb");
     // rows per filter tile: as many as fit next to the shared suffix table (up to 32)
     int R = 32;
-    while (R > 1 && cubical_bwd_rsum_smem(d, T, R) > smem_optin() - 1024) R /= 2;
-    const size_t sm = cubical_bwd_rsum_smem(d, T, R);
+    while (R > 1 && cubical_bwd_rsum_smem(n, d, T, R) > smem_optin() - 1024) R /= 2;
+    const size_t sm = cubical_bwd_rsum_smem(n, d, T, R);
     if (sm > smem_optin() - 1024) return fail(WECT_ERR_UNSUPPORTED, "d x T too large for the adjoint's shared table");
     auto key = std::make_tuple(d, R);
     if (ws.items_bwd_key != key) {
@@ -904,7 +904,9 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
         KL(launch_grid_max_abs(n, d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, ws.M.p, T, ws.range.p, ws.beta.p, st), "setup_range_beta");
-    KL(launch_suffix_rows(dW, ws.S.p, (int64_t)n_grids * d, T, INT64_MAX / d, status, st), "suffix_rows");
+    // the routing kernel sums in int64: 3^n d max|S| must stay below 2^63
+    const int64_t pow3 = n == 1 ? 3 : (n == 2 ? 9 : 27);
+    KL(launch_suffix_rows(dW, ws.S.p, (int64_t)n_grids * d, T, INT64_MAX / ((int64_t)d * pow3), status, st), "suffix_rows");
     KL(launch_octant_sort(n, dirs, d, ws.perm.p, ws.octb.p, st), "octant_sort");
     CubicalBwdArgs a{};
     a.grids = d_grids;
@@ -1301,8 +1303,9 @@ extern "C" wect_status wect_batch_backward_f64(wect_batch b, const double *dirs,
     const int64_t n = (int64_t)b->count * d * T;
     CK(b->ws.Gq.ensure((size_t)n), "alloc");
     CK(b->ws.gscale.ensure(1), "alloc");
-    KL(launch_grad_quantize(G, n, ceil_log2(T) + ceil_log2(d), b->ws.M.p, b->ws.Gq.p, b->ws.gscale.p, b->d_status, st),
-       "grad_quantize");
+    // headroom: suffix sums over T, sums over d directions, signed sums over the 3^n cells of a vertex
+    const int head = ceil_log2(T) + ceil_log2(d) + ceil_log2(b->n == 1 ? 3 : (b->n == 2 ? 9 : 27));
+    KL(launch_grad_quantize(G, n, head, b->ws.M.p, b->ws.Gq.p, b->ws.gscale.p, b->d_status, st), "grad_quantize");
     g_launches++;
     return cubical_backward(b->d_grids, b->count, b->h_grids, b->n, b->wtype, b->frac_bits, b->total_nv, b->ws, dirs, d, T,
                             lo, hi, reinterpret_cast<const int64_t *>(b->ws.Gq.p), 1.0, grad_w, b->d_status, st,

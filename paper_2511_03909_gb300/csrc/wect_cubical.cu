@@ -158,8 +158,7 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
                                            int cv, int hv)
 {
     const int T = P.T;
-    int bt = thi - kMagicBits + nr;
-    bt = min(max(bt, 0), T - 1);
+    const int bt = clamp_bin(thi, nr, T);
     const double h = height3<N>(grid_coord(i0, g.L[0]), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]),
                                 P.dirs + (int64_t)p * N);
     const int be = exact_bin_from(h, P.beta, T, bt);
@@ -249,7 +248,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                 if (!CLAMP) {
                     addr = (uint32_t)thi[j] * D4 + hb[j];
                 } else {
-                    const int b = min(max(thi[j] - kMagicBits + rf[j].nr, 0), T - 1);
+                    const int b = clamp_bin(thi[j], rf[j].nr, T);
                     addr = hb[j] + (uint32_t)b * D4;
                 }
                 if (NSPLIT == 1) {
@@ -283,7 +282,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             const int hvs = (NSPLIT == 2) ? crow[NOCT * CP + oct[j] * CP + i0] : 0;
             int tlo, thi;
             filter_ceil(k0, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
-            const int b = min(max(thi - kMagicBits + rf[j].nr, 0), T - 1);
+            const int b = clamp_bin(thi, rf[j].nr, T);
             const uint32_t addr = histAddr + ((uint32_t)b * (uint32_t)Dt + (uint32_t)col[j]) * 4u;
             if (NSPLIT == 1) {
                 red_shared_add(addr, cvs);
@@ -425,37 +424,147 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 
 // ------------------------------------------------------------------ backward
 
+constexpr int kRsumG = 4;    // directions per group in the adjoint's octant sums
+
+// Slots of the adjoint's direction table: octant-sorted directions, each octant padded to a
+// multiple of kRsumG (an upper bound that does not depend on the octant counts).
+__host__ __device__ inline int rsum_slots(int n, int d)
+{
+    return (d + (1 << n) * (kRsumG - 1) + kRsumG - 1) / kRsumG * kRsumG;
+}
+
+// Byte offsets of the adjoint kernel's shared memory.
+struct RsumLayout {
+    size_t ss, dfil, slotk, tab, flags, total;
+};
+
+__host__ __device__ inline RsumLayout rsum_layout(int n, int d, int T, int R)
+{
+    const int NS = rsum_slots(n, d);
+    RsumLayout l;
+    l.ss = 0;
+    l.dfil = (size_t)(d + 1) * T * 8u;
+    l.slotk = l.dfil + (size_t)d * sizeof(DirFilter);
+    l.tab = (l.slotk + (size_t)NS * 4u + 15u) & ~(size_t)15u;
+    l.flags = l.tab + (size_t)R * NS * 16u;
+    l.total = l.flags + (size_t)R * (NS / kRsumG) + 16u;   // the flag loop reads one group ahead
+    return l;
+}
+
+
 // Per-vertex octant sums of the suffix-scanned upstream gradient,
 //     Rv[o][v] = sum over directions p of octant o of S[p][bin_p(v)]   (octant-major planes),
-// for one item (complex, row range).  Lanes <-> vertices of a row; the direction loop is
-// uniform across the warp and visits the directions octant by octant.  The suffix table of the
-// complex sits in shared memory in octant order ([d][T] int64), the per-(row, direction)
-// filter constants in a [R][d] float4 table (broadcast loads).  Undecided bins are fixed after
-// each group of 8 directions with the exact float64 height.
+// for one item (complex, row range).  Each lane takes two vertices of a row, 32 apart, which
+// share every table load; the direction loop is uniform across the warp and visits the
+// directions octant by octant, kRsumG at a time, two per packed float32x2 filter step.
+//
+// Shared memory: the suffix table of the complex in octant order ([d + 1][T] int64, row d all
+// zero), the direction filters, and per row tile a [R][slots] table of filter constants
+// {S0, Glo, Ghi, W} with the constants of two neighbouring slots interleaved.  Slots are the
+// octant-sorted directions with each octant padded to a multiple of kRsumG; a padding slot has
+// S0 = Glo = Ghi = 0 and reads the zero row.  W is the shared address of the suffix row minus the
+// magic bias, so the candidate bin's entry sits at (thi << 3) + W.  A group flag marks groups
+// whose bins may leave [0, T-1] in that row; they take the clamped path.  Undecided bins are
+// fixed with the exact float64 height.
+// Shared-memory context of one item of the adjoint's octant sums.
+struct RsumCtx {
+    uint32_t ssAddr;              // suffix table [d + 1][T] (row d zero)
+    const int *slotk;             // slot -> octant-sorted direction, -1 for padding
+    const DirFilter *dfil;        // direction filters
+    const int *L;                 // grid sides
+    int T, d;
+};
+
+// Candidate suffix-table addresses of the kRsumG slots of group gi for the two vertices of a lane
+// (k0 = KA, KB packed twice), from the row's filter table at address e.  With clampg the bins
+// are clamped to [0, T-1] (the group may leave the range in this row).  Returns nonzero when a
+// bin is undecided; with non-null t/h it also returns the filter ends.
+template <int N>
+__device__ __forceinline__ int rsum_group(uint32_t e, int gi, bool clampg, F2 KA, F2 KB, F2 M2, const RsumCtx &C,
+                                          int i1, int i2, uint32_t *adA, uint32_t *adB, int *tAo, int *hAo,
+                                          int *tBo, int *hBo)
+{
+    constexpr int G = kRsumG;
+    int hA[G], hB[G];
+    int bad = 0;
+#pragma unroll
+    for (int u = 0; u < G; u += 2) {
+        unsigned long long s0, gl, gh, ww;
+        lds_v2u64(e + u * 16u, s0, gl);
+        lds_v2u64(e + u * 16u + 16u, gh, ww);
+        int t0, t1, t2, t3;
+        filter_ceil2(KA, F2{s0}, F2{gl}, F2{gh}, M2, t0, hA[u], t1, hA[u + 1]);
+        filter_ceil2(KB, F2{s0}, F2{gl}, F2{gh}, M2, t2, hB[u], t3, hB[u + 1]);
+        bad |= (t0 ^ hA[u]) | (t1 ^ hA[u + 1]) | (t2 ^ hB[u]) | (t3 ^ hB[u + 1]);
+        if (tAo) {
+            tAo[u] = t0;
+            tAo[u + 1] = t1;
+            tBo[u] = t2;
+            tBo[u + 1] = t3;
+        }
+        const uint32_t w0 = (uint32_t)ww, w1 = (uint32_t)(ww >> 32);
+        adA[u] = ((uint32_t)hA[u] << 3) + w0;
+        adA[u + 1] = ((uint32_t)hA[u + 1] << 3) + w1;
+        adB[u] = ((uint32_t)hB[u] << 3) + w0;
+        adB[u + 1] = ((uint32_t)hB[u + 1] << 3) + w1;
+    }
+    if (clampg) {
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int k = C.slotk[gi * G + u];
+            int nr = 0, kr = C.d;
+            if (k >= 0) {
+                nr = make_row_filter<N>(C.dfil[k], i1, i2, C.L).nr;
+                kr = k;
+            }
+            const uint32_t rowAddr = C.ssAddr + 8u * (uint32_t)(kr * C.T);
+            adA[u] = rowAddr + 8u * (uint32_t)(k >= 0 ? clamp_bin(hA[u], nr, C.T) : 0);
+            adB[u] = rowAddr + 8u * (uint32_t)(k >= 0 ? clamp_bin(hB[u], nr, C.T) : 0);
+        }
+    }
+    if (hAo) {
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            hAo[u] = hA[u];
+            hBo[u] = hB[u];
+        }
+    }
+    return bad;
+}
+
 template <int N>
 __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const CubicalBwdArgs P)
 {
     constexpr int NOCT = 1 << N;
-    constexpr int G = 4;
+    constexpr int G = kRsumG;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sb[NOCT + 1];
     const int T = P.T, d = P.d, RB = P.R;
+    const int NS = rsum_slots(N, d), NG = NS / G;
+    const RsumLayout lay = rsum_layout(N, d, T, RB);
+    long long *Ss = reinterpret_cast<long long *>(smem + lay.ss);
+    DirFilter *dfil = reinterpret_cast<DirFilter *>(smem + lay.dfil);
+    int *slotk = reinterpret_cast<int *>(smem + lay.slotk);
+    uint8_t *flags = smem + lay.flags;
+    const uint32_t ssAddr = smem_addr(Ss), tabAddr = smem_addr(smem + lay.tab);
     const WorkItem W = P.items[blockIdx.x];
     const GridDesc g = P.grids[W.cx];
     const int L0 = g.L[0], L1 = g.L[1];
-    long long *Ss = reinterpret_cast<long long *>(smem);                 // [d][T], octant order
-    DirFilter *dfil = reinterpret_cast<DirFilter *>(Ss + (size_t)d * T);  // [d]
-    float4 *rowf = reinterpret_cast<float4 *>(                             // [RB][d]
-        smem + (((size_t)d * T * 8 + (size_t)d * sizeof(DirFilter) + 15) & ~(size_t)15));
-    __shared__ int octb[9];
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
     const long long *S = reinterpret_cast<const long long *>(P.S) + (int64_t)W.cx * d * T;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
-    uint32_t *clampw = reinterpret_cast<uint32_t *>(rowf + (size_t)RB * d);    // [RB*d/32] bit per (row, direction)
 
-    if (tid <= NOCT) octb[tid] = P.octb[tid];
-    for (int idx = tid; idx < d * T; idx += blockDim.x) {
+    if (tid == 0) {
+        int s = 0;
+        for (int o = 0; o < NOCT; ++o) {
+            sb[o] = s;
+            s += (P.octb[o + 1] - P.octb[o] + G - 1) / G * G;
+        }
+        sb[NOCT] = s;
+    }
+    for (int idx = tid; idx < (d + 1) * T; idx += blockDim.x) {
         const int k = idx / T, q = idx - k * T;
-        Ss[idx] = S[(int64_t)P.perm[k] * T + q];
+        Ss[idx] = (k < d) ? S[(int64_t)P.perm[k] * T + q] : 0ll;
     }
     for (int k = tid; k < d; k += blockDim.x) {
         const int p = P.perm[k];
@@ -464,126 +573,224 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
         for (int a = 0; a < N; ++a) sv[a] = P.dirs[(int64_t)p * N + a];
         dfil[k] = make_dir_filter<N>(sv, g.L, lo, hi, step, T);
     }
-    const int segs = (L0 + 31) >> 5;
+    __syncthreads();
+    for (int j = tid; j < NS; j += blockDim.x) {
+        int k = -1;
+        for (int o = 0; o < NOCT; ++o)
+            if (j >= sb[o] && j < sb[o + 1] && P.octb[o] + (j - sb[o]) < P.octb[o + 1]) k = P.octb[o] + (j - sb[o]);
+        slotk[j] = k;
+    }
+    const int segs = (L0 + 63) >> 6;
+    const uint32_t zeroW = ssAddr + 8u * (uint32_t)(d * T) - 8u * (uint32_t)kMagicBits;
+    const RsumCtx C{ssAddr, slotk, dfil, g.L, T, d};
     for (int rt = W.r0; rt < W.r1; rt += RB) {
         const int nrt = min(RB, W.r1 - rt);
         __syncthreads();
-        for (int i = tid; i < (RB * d + 31) / 32; i += blockDim.x) clampw[i] = 0;
-        __syncthreads();
-        for (int idx = tid; idx < nrt * d; idx += blockDim.x) {
-            const int rl = idx / d, k = idx - rl * d;
-            const int r = rt + rl;
-            const DirFilter f = dfil[k];
-            const RowFilter rf = make_row_filter<N>(f, r % L1, r / L1, g.L);
-            // bins of the whole row provably inside [0, T-1]?  (as in the forward kernel)
-            const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
-            const float lowf = __fadd_rd(__fsub_rd(rf.Glo, A), (float)(rf.nr - 1));
-            const float highf = __fadd_ru(__fadd_ru(rf.Ghi, A), (float)(rf.nr + 1));
-            const bool inr = (lowf >= 0.0f) && (highf <= (float)(T - 1));
-            rowf[rl * d + k] = make_float4(rf.Glo, rf.Ghi, f.S0, __int_as_float(rf.nr - kMagicBits));
-            if (!inr) atomicOr(&clampw[(rl * d + k) >> 5], 1u << ((rl * d + k) & 31));
+        // filter table of the row tile: one warp per row, lanes over slots
+        for (int rl = wid; rl < nrt; rl += nwarps) {
+            const int r = rt + rl, i1 = r % L1, i2 = r / L1;
+            for (int j0 = 0; j0 < NS; j0 += 32) {
+                const int j = j0 + lane;
+                const int k = (j < NS) ? slotk[j] : -1;
+                float S0 = 0.f, Glo = 0.f, Ghi = 0.f;
+                uint32_t Wj = zeroW;
+                unsigned cf = 0;
+                if (k >= 0) {
+                    const DirFilter f = dfil[k];
+                    const RowFilter rf = make_row_filter<N>(f, i1, i2, g.L);
+                    // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
+                    const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
+                    const float lowf = __fadd_rd(__fsub_rd(rf.Glo, A), (float)(rf.nr - 1));
+                    const float highf = __fadd_ru(__fadd_ru(rf.Ghi, A), (float)(rf.nr + 1));
+                    cf = (!(lowf >= 0.0f) || !(highf <= (float)(T - 1))) ? 1u : 0u;
+                    S0 = f.S0;
+                    Glo = rf.Glo;
+                    Ghi = rf.Ghi;
+                    Wj = ssAddr + 8u * (uint32_t)(k * T + rf.nr) - 8u * (uint32_t)kMagicBits;
+                }
+                cf |= __shfl_xor_sync(0xffffffffu, cf, 1);
+                cf |= __shfl_xor_sync(0xffffffffu, cf, 2);
+                if (j < NS) {
+                    float *e = reinterpret_cast<float *>(smem + lay.tab + ((size_t)rl * NS + (j & ~1)) * 16u);
+                    const int h = j & 1;
+                    e[h] = S0;
+                    e[2 + h] = Glo;
+                    e[4 + h] = Ghi;
+                    reinterpret_cast<uint32_t *>(e)[6 + h] = Wj;
+                    if ((j & (G - 1)) == 0) flags[rl * NG + j / G] = (uint8_t)cf;
+                }
+            }
         }
         __syncthreads();
         for (int job = wid; job < nrt * segs; job += nwarps) {
             const int rl = job / segs, seg = job - rl * segs;
-            const int i0 = min(seg * 32 + lane, L0 - 1);
-            const bool live = seg * 32 + lane < L0;
+            // two vertices per lane, 32 apart in the row
+            const int ia = min(seg * 64 + lane, L0 - 1), ib = min(seg * 64 + 32 + lane, L0 - 1);
+            const bool liveA = seg * 64 + lane < L0, liveB = seg * 64 + 32 + lane < L0;
             const int r = rt + rl, i1 = r % L1, i2 = r / L1;
-            const float kk = (float)(2 * i0 - (L0 - 1));
-            const float4 *rf = rowf + rl * d;
-            const int64_t vout = g.v_off + (int64_t)i0 + (int64_t)L0 * r;
+            const float ka = (float)(2 * ia - (L0 - 1)), kb = (float)(2 * ib - (L0 - 1));
+            const F2 KA = f2_pack(ka, ka), KB = f2_pack(kb, kb), M2 = f2_pack(kMagic, kMagic);
+            const uint32_t rowTab = tabAddr + (uint32_t)(rl * NS) * 16u;
+            const uint8_t *rowFlags = flags + rl * NG;
+            const int64_t voutA = g.v_off + (int64_t)ia + (int64_t)L0 * r;
 #pragma unroll 1
             for (int o = 0; o < NOCT; ++o) {
-                long long a = 0;
-                const int kb = octb[o], ke = octb[o + 1];
-                int k0 = kb;
-                // full groups of G directions: filter loads first, then bins and gathers
-                for (; k0 + G <= ke; k0 += G) {
-                    float4 f[G];
+                long long accA = 0, accB = 0;
+                const int g0 = sb[o] / G, g1 = sb[o + 1] / G;
+                int badOct = 0;
+                // fast pass: no vote and no flag load on the critical path (the next group's
+                // clamp flag is fetched one group ahead)
+                uint8_t fnext = rowFlags[g0];
+#pragma unroll 1
+                for (int gi = g0; gi < g1; ++gi) {
+                    const bool clampg = fnext != 0;
+                    fnext = rowFlags[gi + 1];
+                    uint32_t adA[G], adB[G];
+                    badOct |= rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, clampg, KA, KB, M2, C, i1, i2, adA,
+                                            adB, nullptr, nullptr, nullptr, nullptr);
 #pragma unroll
-                    for (int u = 0; u < G; ++u) f[u] = rf[k0 + u];
-                    // any direction of the group whose row may leave the threshold range?
-                    const int bit = rl * d + k0;
-                    const uint32_t cw = ((clampw[bit >> 5] >> (bit & 31)) |
-                                         ((bit & 31) + G > 32 ? clampw[(bit >> 5) + 1] << (32 - (bit & 31)) : 0u)) &
-                                        ((1u << G) - 1u);
-                    int bt[G];
-                    int bad = 0;
-                    if (cw == 0) {
-#pragma unroll
-                        for (int u = 0; u < G; ++u) {
-                            int tlo, thi;
-                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
-                            bad |= tlo ^ thi;
-                            bt[u] = thi + __float_as_int(f[u].w);
-                        }
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < G; ++u) {
-                            int tlo, thi;
-                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
-                            bad |= tlo ^ thi;
-                            bt[u] = min(max(thi + __float_as_int(f[u].w), 0), T - 1);
-                        }
+                    for (int u = 0; u < G; ++u) {
+                        accA += lds_s64(adA[u]);
+                        accB += lds_s64(adB[u]);
                     }
-#pragma unroll
-                    for (int u = 0; u < G; ++u) a += Ss[(k0 + u) * T + bt[u]];
-                    if (__any_sync(0xffffffffu, bad != 0)) {
+                }
+                if (__any_sync(0xffffffffu, badOct != 0)) {
+                    // undecided bins somewhere in this octant: replace their candidate entries
+                    // by the entries of the exact float64 bins
+#pragma unroll 1
+                    for (int gi = g0; gi < g1; ++gi) {
+                        uint32_t adA[G], adB[G];
+                        int tA[G], hA[G], tB[G], hB[G];
+                        if (!rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, rowFlags[gi] != 0, KA, KB, M2, C, i1,
+                                           i2, adA, adB, tA, hA, tB, hB))
+                            continue;
 #pragma unroll
                         for (int u = 0; u < G; ++u) {
-                            int tlo, thi;
-                            filter_ceil(kk, f[u].z, f[u].x, f[u].y, tlo, thi);
-                            if (tlo != thi) {
-                                const int k = k0 + u;
-                                const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]),
-                                                            grid_coord(i2, g.L[2]), P.dirs + (int64_t)P.perm[k] * N);
-                                const int be = exact_bin_from(h, P.beta, T, bt[u]);
-                                a += Ss[k * T + be] - Ss[k * T + bt[u]];
+                            const int k = slotk[gi * G + u];
+                            if (k < 0) continue;
+                            const double *sp = P.dirs + (int64_t)P.perm[k] * N;
+                            if (tA[u] != hA[u]) {
+                                const int cand = (int)((adA[u] - ssAddr) >> 3) - k * T;
+                                const double h = height3<N>(grid_coord(ia, L0), grid_coord(i1, g.L[1]),
+                                                            grid_coord(i2, g.L[2]), sp);
+                                accA += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adA[u]);
+                            }
+                            if (tB[u] != hB[u]) {
+                                const int cand = (int)((adB[u] - ssAddr) >> 3) - k * T;
+                                const double h = height3<N>(grid_coord(ib, L0), grid_coord(i1, g.L[1]),
+                                                            grid_coord(i2, g.L[2]), sp);
+                                accB += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adB[u]);
                             }
                         }
                     }
                 }
-                // remainder, one direction at a time
-                for (; k0 < ke; ++k0) {
-                    const float4 f = rf[k0];
-                    int tlo, thi;
-                    filter_ceil(kk, f.z, f.x, f.y, tlo, thi);
-                    int b = min(max(thi + __float_as_int(f.w), 0), T - 1);
-                    if (tlo != thi) {
-                        const double h = height3<N>(grid_coord(i0, L0), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]),
-                                                    P.dirs + (int64_t)P.perm[k0] * N);
-                        b = exact_bin_from(h, P.beta, T, b);
-                    }
-                    a += Ss[k0 * T + b];
-                }
-                if (live) P.Rv[(int64_t)o * P.total_nv + vout] = a;
+                if (liveA) P.Rv[(int64_t)o * P.total_nv + voutA] = accA;
+                if (liveB) P.Rv[(int64_t)o * P.total_nv + voutA + 32] = accB;
             }
         }
     }
 }
 
-// Route each cell's gradient to its heaviest vertex and sum exactly (128-bit):
+// Route each cell's gradient to its heaviest vertex:
 //     I_v = sum over cells s containing v whose heaviest vertex is v (ties -> lowest index) of
 //           (-1)^dim(s) sum_o Rv[o][corner_o(s)].
-// The neighbours that beat v (heavier, or as heavy with a lower index) form a bit mask over the
-// 3^n neighbourhood; v is the heaviest vertex of a cell iff the mask misses every cell vertex.
+// Cells containing v are indexed like the 3^n neighbourhood: e in {-1,0,1}^n spans v and v + e.
+// The neighbours that beat v (heavier, or as heavy with a lower index) form a bit mask; v is
+// the heaviest vertex of a cell iff the mask misses every cell vertex, which gives the mask A
+// of the cells v takes.  Under octant o (sg_a = +1 when bit a is set, else -1) the corner of a
+// cell e is v + delta * sg with delta_a = [e_a == sg_a], so regrouping by (o, delta),
+//     I_v = sum_o sum_delta K[o][delta] * Rv[o][v + delta * sg],
+//     K[o][delta] = #(A & even cells of the class) - #(A & odd cells of the class),
+// where the class of (o, delta) is the cells with e_a = sg_a on delta and e_a in {0, -sg_a}
+// off it.  That is 2^n x 2^n coalesced loads per vertex and no divergence.  Every partial sum is
+// a signed sum over at most 3^n cells of sums over disjoint direction sets, so with
+// 3^n d max|S| < 2^63 (checked when the suffix table is built) int64 is exact.
+__host__ __device__ constexpr int route_nb(int n) { return n == 1 ? 3 : (n == 2 ? 9 : 27); }
+
+// Vertex mask (over the 3^n neighbourhood) of the cell with extent vector e = cell index t.
+__host__ __device__ constexpr uint32_t route_cell_mask(int n, int t)
+{
+    uint32_t m = 0;
+    for (int sub = 0; sub < (1 << n); ++sub) {
+        int idx = 0, mul = 1;
+        bool ok = true;
+        for (int a = 0; a < n; ++a) {
+            const int ea = (t / mul) % 3 - 1;
+            int f = 0;
+            if ((sub >> a) & 1) {
+                if (ea == 0) ok = false;
+                f = ea;
+            }
+            idx += (f + 1) * mul;
+            mul *= 3;
+        }
+        if (ok) m |= 1u << idx;
+    }
+    return m;
+}
+
+// Cells of the class (o, delta) with even (par = 0) or odd (par = 1) dimension.
+__host__ __device__ constexpr uint32_t route_class_mask(int n, int o, int delta, int par)
+{
+    uint32_t m = 0;
+    for (int t = 0; t < route_nb(n); ++t) {
+        int mul = 1, dim = 0;
+        bool in = true;
+        for (int a = 0; a < n; ++a) {
+            const int ea = (t / mul) % 3 - 1;
+            const int sg = ((o >> a) & 1) ? 1 : -1;
+            dim += ea != 0;
+            if ((delta >> a) & 1) in = in && ea == sg;
+            else in = in && ea != sg;
+            mul *= 3;
+        }
+        if (in && (dim & 1) == par) m |= 1u << t;
+    }
+    return m;
+}
+
+// Neighbourhood index of the corner v + delta * sg(o).
+__host__ __device__ constexpr int route_corner(int n, int o, int delta)
+{
+    int idx = 0, mul = 1;
+    for (int a = 0; a < n; ++a) {
+        const int c = ((delta >> a) & 1) ? (((o >> a) & 1) ? 1 : -1) : 0;
+        idx += (c + 1) * mul;
+        mul *= 3;
+    }
+    return idx;
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwdArgs P)
 {
     constexpr int NOCT = 1 << N;
-    constexpr int NB = (N == 1) ? 3 : (N == 2) ? 9 : 27;
+    constexpr int NB = route_nb(N);
     constexpr int CENTER = (NB - 1) / 2;
     const int64_t gid = P.v_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= P.v_end) return;
-    int lo_c = 0, hi_c = P.n_grids - 1;
-    while (lo_c < hi_c) {
-        const int mid = (lo_c + hi_c + 1) >> 1;
-        if (P.grids[mid].v_off <= gid) lo_c = mid; else hi_c = mid - 1;
+    int cx = 0;
+    if (P.n_grids > 1) {
+        int hi_c = P.n_grids - 1;
+        while (cx < hi_c) {
+            const int mid = (cx + hi_c + 1) >> 1;
+            if (P.grids[mid].v_off <= gid) cx = mid; else hi_c = mid - 1;
+        }
     }
-    const GridDesc g = P.grids[lo_c];
+    const GridDesc g = P.grids[cx];
     const int64_t v = gid - g.v_off;
     const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
-    const int i0 = (int)(v % L0), i1 = (int)((v / L0) % L1), i2 = (int)(v / ((int64_t)L0 * L1));
+    int i0, i1, i2;
+    if (g.nv <= 0x7fffffff) {
+        const uint32_t v32 = (uint32_t)v, q = v32 / (uint32_t)L0;
+        i0 = (int)(v32 - q * (uint32_t)L0);
+        i1 = (int)(q % (uint32_t)L1);
+        i2 = (int)(q / (uint32_t)L1);
+    } else {
+        i0 = (int)(v % L0);
+        i1 = (int)((v / L0) % L1);
+        i2 = (int)(v / ((int64_t)L0 * L1));
+    }
     const int32_t *wp = g.w + v;
     const int32_t wv = __ldg(wp);
     // neighbour offsets (flat, int32), in-bounds mask and "beats v" mask over the 3^n neighbourhood
@@ -604,51 +811,26 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
             }
         }
     }
-    const long long *Rp[NOCT];
+    // cells v takes: in bounds (the far corner v + e is) and beaten nowhere
+    uint32_t A = 0;
 #pragma unroll
-    for (int o = 0; o < NOCT; ++o) Rp[o] = reinterpret_cast<const long long *>(P.Rv) + (int64_t)o * P.total_nv + gid;
-    int64_t Ihi = 0;
-    uint64_t Ilo = 0;
+    for (int t = 0; t < NB; ++t)
+        if ((okm >> t) & 1u)
+            if ((beat & route_cell_mask(N, t)) == 0) A |= 1u << t;
+    long long acc = 0;
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-        const int dlt[3] = {t % 3 - 1, (N >= 2) ? (t / 3) % 3 - 1 : 0, (N >= 3) ? t / 9 - 1 : 0};
-        // vertex mask of the cell spanning v and v + dlt (compile-time)
-        uint32_t cm = 0;
+    for (int o = 0; o < NOCT; ++o) {
+        const long long *R = reinterpret_cast<const long long *>(P.Rv) + (int64_t)o * P.total_nv + gid;
 #pragma unroll
-        for (int sm = 0; sm < NOCT; ++sm) {
-            int f[3] = {0, 0, 0};
-            bool ok = true;
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                if ((sm >> a) & 1) {
-                    if (dlt[a] == 0) ok = false;
-                    f[a] = dlt[a];
-                }
-            }
-            if (ok) cm |= 1u << ((f[0] + 1) + (N >= 2 ? 3 * (f[1] + 1) : 0) + (N >= 3 ? 9 * (f[2] + 1) : 0));
+        for (int dl = 0; dl < NOCT; ++dl) {
+            const int K = __popc(A & route_class_mask(N, o, dl, 0)) - __popc(A & route_class_mask(N, o, dl, 1));
+            // K == 0 whenever the corner lies outside the grid (every cell of the class holds it)
+            const long long r = (K != 0) ? __ldg(R + off[route_corner(N, o, dl)]) : 0ll;
+            acc += (long long)K * r;
         }
-        if ((okm & (1u << t)) == 0 || (beat & cm) != 0) continue;
-        // g(cell) = sum_o Rv[o][sign corner under octant o]
-        long long gs = 0;
-#pragma unroll
-        for (int o = 0; o < NOCT; ++o) {
-            int c[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < N; ++a)
-                if (dlt[a] != 0) c[a] = ((o >> a) & 1) ? max(dlt[a], 0) : min(dlt[a], 0);
-            const int ci = (c[0] + 1) + (N >= 2 ? 3 * (c[1] + 1) : 0) + (N >= 3 ? 9 * (c[2] + 1) : 0);
-            gs += __ldg(Rp[o] + off[ci]);
-        }
-        int dimc = 0;
-#pragma unroll
-        for (int a = 0; a < N; ++a) dimc += (dlt[a] != 0);
-        if (dimc & 1) gs = -gs;
-        const uint64_t old = Ilo;
-        Ilo += (uint64_t)gs;
-        Ihi += (gs < 0 ? -1 : 0) + (Ilo < old ? 1 : 0);
     }
     const double scale = P.scale_dev ? *P.scale_dev : P.scale;
-    P.grad[gid] = (float)(i128_to_double(Ihi, Ilo) * scale);
+    P.grad[gid] = (float)((double)acc * scale);
 }
 
 // ------------------------------------------------------------------ ECF on a grid (one vertex filter)
@@ -808,10 +990,9 @@ cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size
     return cudaGetLastError();
 }
 
-size_t cubical_bwd_rsum_smem(int d, int T, int R)
+size_t cubical_bwd_rsum_smem(int n, int d, int T, int R)
 {
-    const size_t a = (size_t)d * T * 8u + (size_t)d * sizeof(DirFilter);
-    return ((a + 15) & ~(size_t)15) + (size_t)R * d * sizeof(float4) + (size_t)((R * d + 31) / 32 + 1) * 4u;
+    return rsum_layout(n, d, T, R).total;
 }
 
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,

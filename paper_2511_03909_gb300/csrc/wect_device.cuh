@@ -129,8 +129,13 @@ __device__ __forceinline__ DirFilter make_dir_filter(const double *s, const int 
     f.oct = 0;
     for (int a = 0; a < N; ++a)
         if (s[a] > 0.0) f.oct |= 1 << a;
-    if (!(step > 0.0)) {
-        // degenerate range: force the exact path everywhere
+    double sumabs = 0.0;
+    for (int a = 0; a < N; ++a) sumabs += fabs(s[a]);
+    // |u| <= big for every vertex: the float32 filter is sound while big stays well inside the
+    // magic-constant range (|u| < 2^22); beyond 2^21 every bin takes the exact path
+    const double big = (step > 0.0) ? (double)T + (fabs(lo) + fabs(hi) + sumabs) / step + 1.0 : 0.0;
+    if (!(step > 0.0) || !(big <= 0x1p21)) {
+        // degenerate or very narrow range: force the exact path everywhere
         f.S0 = 0.f;
         f.B1 = f.B2 = f.C = DS{0.f, 0.f};
         f.eta = __int_as_float(0x7f800000);
@@ -143,9 +148,6 @@ __device__ __forceinline__ DirFilter make_dir_filter(const double *s, const int 
     f.B1 = ds_from_double(b1);
     f.B2 = ds_from_double(b2);
     f.C = ds_from_double(__ddiv_rn(-lo, step));
-    double sumabs = 0.0;
-    for (int a = 0; a < N; ++a) sumabs += fabs(s[a]);
-    double big = (double)T + (fabs(lo) + fabs(hi) + sumabs) / step + 1.0;
     double A0 = fabs((double)f.S0) * (double)(L[0] > 1 ? L[0] - 1 : 0);
     double eta = (1.0 + 0x1p-10) * (0x1p-25 + A0 * 0x1p-24) + 0x1p-40 * big;
     f.eta = __double2float_ru(eta);
@@ -181,6 +183,13 @@ __device__ __forceinline__ void filter_ceil(float k0, float S0, float Glo, float
     float uh = __fmaf_ru(k0, S0, Ghi);
     tlo = __float_as_int(__fadd_ru(ul, kMagic));
     thi = __float_as_int(__fadd_ru(uh, kMagic));
+}
+
+// Candidate bin from the upper end of the filter, clamped to [0, T-1].  A negative thi is a
+// negative float32 sum, i.e. u far below the range (bin 0).
+__device__ __forceinline__ int clamp_bin(int thi, int nr, int T)
+{
+    return thi < 0 ? 0 : min(max(thi - kMagicBits + nr, 0), T - 1);
 }
 
 // Two directions at once with the packed float32 pipe (sm_100+ f32x2): element-wise the same
@@ -241,6 +250,18 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, int32_t v)
 __device__ __forceinline__ void red_shared_add_u32(uint32_t addr, uint32_t v)
 {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+__device__ __forceinline__ void lds_v2u64(uint32_t addr, unsigned long long &a, unsigned long long &b)
+{
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+
+__device__ __forceinline__ long long lds_s64(uint32_t addr)
+{
+    long long v;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
 }
 
 __device__ __forceinline__ int4 lds128(uint32_t addr)

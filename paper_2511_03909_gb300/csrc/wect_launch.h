@@ -66,7 +66,7 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0);
 int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
 cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
-size_t cubical_bwd_rsum_smem(int d, int T, int R);
+size_t cubical_bwd_rsum_smem(int n, int d, int T, int R);
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
                                unsigned long long *out, int64_t nv, cudaStream_t st);
 cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,

@@ -27,8 +27,9 @@ __global__ void dir_filter_kernel(const double *__restrict__ dirs, int d, int T,
     if (p >= d) return;
     const double lo = range[0], step = range[2];
     float Af[3] = {0.f, 0.f, 0.f}, Cf = 0.f, eta = __int_as_float(0x7f800000);
+    double U = 0.0;
     if (step > 0.0) {
-        double U = fabs(lo) / step;
+        U = fabs(lo) / step;
         for (int a = 0; a < N; ++a) {
             const double A = __ddiv_rn(dirs[(int64_t)p * N + a], step);
             Af[a] = __double2float_rn(A);
@@ -38,6 +39,12 @@ __global__ void dir_filter_kernel(const double *__restrict__ dirs, int d, int T,
         // coordinate and coefficient roundings (2^-24 |x_a A_a| each) and N+1 fma/constant roundings
         // (2^-24 of a partial sum <= U): |u_f32 - u| <= 2^-24 (N+3) U; 25% margin
         eta = __double2float_ru(0x1p-24 * 1.25 * (double)(N + 3) * (U + 1.0) + 0x1p-40 * ((double)T + U));
+    }
+    // |u| <= U: beyond 2^21 (or a zero step) the magic-constant ceiling is not sound, so every
+    // bin takes the exact path (u = 0, eta = inf)
+    if (!(step > 0.0) || !(U + (double)T <= 0x1p21)) {
+        Af[0] = Af[1] = Af[2] = Cf = 0.f;
+        eta = __int_as_float(0x7f800000);
     }
     float4 *t = reinterpret_cast<float4 *>(tab + (int64_t)p * 8);
     t[0] = make_float4(Af[0], Af[1], Af[2], Cf);
@@ -76,14 +83,13 @@ __global__ void __launch_bounds__(256) vertex_bins_kernel(const double *__restri
         for (int a = N - 1; a >= 0; --a) u = __fmaf_rn(__ldg(xf + v * N + a), Af[a], u);
         const int tlo = __float_as_int(__fadd_ru(__fsub_rd(u, eta), kMagic));
         const int thi = __float_as_int(__fadd_ru(__fadd_ru(u, eta), kMagic));
-        int b = thi - kMagicBits;
+        int b = clamp_bin(thi, 0, T);
         if (tlo != thi) {
             double xd[3] = {0.0, 0.0, 0.0};
             for (int a = 0; a < N; ++a) xd[a] = coords[v * N + a];
             const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
             b = exact_bin_from(h, beta, T, b);
         }
-        b = min(max(b, 0), T - 1);
         if (act) bins[v * Dt + col] = (uint16_t)b;
     }
 }
