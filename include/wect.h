@@ -171,10 +171,12 @@ WECT_API wect_status ecf_compute(wect_complex cx, const double *filter, int T, d
  *   I_v      = sum over cells s whose heaviest vertex is v of (-1)^dim(s) g(s)
  *              (ties of the heaviest vertex go to the lowest vertex index)
  *   grad_w[v] = (float)((double)I_v * scale)
- * I_v is accumulated exactly (128-bit); the per-direction sums S and g(s) are int64, so the
- * upstream must satisfy d * max_q |S[p][q]| < 2^63 (else WECT_ERR_OVERFLOW is set in the device
- * status word and grad_w is unspecified).  Only complexes whose cell weights are the max of
- * their vertex weights (cubical, or simplicial in MAX_OF_VERTICES mode) are supported.
+ * All sums are exact integers.  On a simplicial complex I_v is accumulated in 128 bits and the
+ * upstream must satisfy d * max_q |S[p][q]| < 2^63.  On a cubical grid every partial sum of I_v
+ * is int64, and the bound is 3^n * d * max_q |S[p][q]| < 2^63, because a vertex lies in 3^n
+ * cells.  When the bound fails, WECT_ERR_OVERFLOW is set in the device status word and grad_w
+ * is unspecified.  Only complexes whose cell weights are the max of their vertex weights
+ * (cubical, or simplicial in MAX_OF_VERTICES mode) are supported.
  *   dW (dev)      [d][T] int64 upstream gradient in fixed-point units
  *   grad_w (dev)  [k_0] float32
  */
@@ -226,8 +228,9 @@ WECT_API wect_status wect_batch_backward(wect_batch b, const double *dirs, int d
  * Adjoint of wect_batch_compute for a float64 upstream gradient G = dL/dW (dev [count][d][T])
  * with W in real units (the fixed-point table times 2^-frac_bits), so grad_w[v] = dL/dw_v for
  * the real-valued vertex weights.  G is quantised on the device to int64 with the largest
- * power-of-two scale 2^k that keeps d * T * max|G| * 2^k below 2^62 (exact when G's values are
- * multiples of 2^-k, as for the gradient of a squared error between fixed-point transforms);
+ * power-of-two scale 2^k that keeps 3^n * d * T * max|G| * 2^k below 2^62, the headroom of the
+ * int64 adjoint (exact when G's values are multiples of 2^-k, as for the gradient of a squared
+ * error between fixed-point transforms);
  * the rest is wect_batch_backward.  Asynchronous: no host synchronisation.
  */
 WECT_API wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
