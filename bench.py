@@ -142,10 +142,13 @@ def _traffic_per_launch():
     the kernel source changed since the counters were taken."""
     import hashlib
 
-    src = os.path.join(ROOT, "paper_2511_03909_gb300", "csrc", "wect_cubical.cu")
+    csrc = os.path.join(ROOT, "paper_2511_03909_gb300", "csrc")
     prof = os.path.join(ROOT, "profiles", "cubical_fwd_voxel3d_128.md")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        hs = hashlib.sha256()
+        for name in ("wect_cubical.cu", "wect_device.cuh"):     # the forward kernel's sources
+            hs.update(open(os.path.join(csrc, name), "rb").read())
+        h = hs.hexdigest()[:16]
         for ln in open(prof):
             if ln.startswith("traffic_bytes_per_launch:"):
                 _, val, _, sha = ln.split()

@@ -400,7 +400,7 @@ class WECTFunction(torch.autograd.Function):
         batch.set_weights(w.detach().contiguous())
         W = batch.wect(dirs, T, lo, hi)
         ctx.batch, ctx.dirs, ctx.T, ctx.lo, ctx.hi = batch, dirs, T, lo, hi
-        return torch.ldexp(W.to(torch.float64), torch.tensor(-batch.frac_bits, device=W.device, dtype=torch.int32))
+        return W.to(torch.float64) * (2.0 ** -batch.frac_bits)     # exact: a power of two
 
     @staticmethod
     def backward(ctx, gW: torch.Tensor):
