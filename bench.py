@@ -410,6 +410,43 @@ def extras(P, S, dev):
     return res
 
 
+def run_case(name):
+    """Run one small workload a few times, untimed, for ncu captures of kernels the headline
+    step does not launch (the adjoint and the simplicial gather)."""
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import paper_2511_03909_gb300 as P
+    import synthetic as S
+
+    dev = torch.device("cuda:0")
+    if name == "adjoint16":
+        # 16 volumes 64^3 f32 (2^-24 fixed point), d = 128 Fibonacci, T = 128: three adjoint calls
+        wv = S.volume_batch_diff(count=16)
+        dirs = torch.from_numpy(wv.dirs).to(dev)
+        bt = P.CubicalBatch(flat=torch.from_numpy(wv.target.reshape(-1)).to(dev), dims=[wv.dims] * 16, frac_bits=24)
+        bb = P.CubicalBatch(flat=torch.from_numpy(wv.grids.reshape(-1)).to(dev), dims=[wv.dims] * 16, frac_bits=24)
+        D = (bb.wect(dirs, wv.T, wv.lo, wv.hi) - bt.wect(dirs, wv.T, wv.lo, wv.hi)).contiguous()
+        for _ in range(3):
+            g = bb.backward(dirs, wv.T, wv.lo, wv.hi, D, 2.0 ** -23 / D.numel())
+        torch.cuda.synchronize()
+        print("adjoint16 ok", float(g.abs().sum()))
+    elif name == "mesh64":
+        # the 1024^2 mesh with d = 64 directions (two 32-direction tiles), T = 512, range [-1.5, 1.5]
+        wl = S.mesh2d_1024(d=64)
+        cx = wl.complex
+        h = P.SimplicialComplex(torch.from_numpy(cx.coords).to(dev), [torch.from_numpy(x).to(dev) for x in cx.simplices],
+                                torch.from_numpy(cx.weights).to(dev), frac_bits=24)
+        dirs = torch.from_numpy(wl.dirs).to(dev)
+        for _ in range(2):
+            W = h.wect(dirs, wl.T, -1.5, 1.5)
+        torch.cuda.synchronize()
+        print("mesh64 ok", int(W[:, -1].abs().sum()))
+    else:
+        raise SystemExit(f"unknown case {name}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,7 +455,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", action="store_true", help="also time the batched and differentiation workloads")
+    ap.add_argument("--case", choices=["adjoint16", "mesh64"],
+                    help="run one untimed workload for an ncu capture (no JSON line)")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
