@@ -374,6 +374,7 @@ struct CubLaunch {
     int64_t climit;
     const GridDesc *d_grids;
     Workspace *ws;
+    int *status;                  // device status word (non-finite directions are flagged here)
 };
 
 // Enqueue the forward transform of a set of grids: [range], beta, work queue, stencil kernel,
@@ -387,10 +388,10 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
         CK(cudaMemsetAsync(ws.M.p, 0, sizeof(unsigned long long), st), "memset");
         KL(launch_grid_max_abs(L.n, L.d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
     }
-    KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, ws.M.p, T, ws.range.p, ws.beta.p, st), "setup_range_beta");
-    KL(launch_octant_sort(L.n, dirs, d, ws.perm.p, ws.octb.p, st), "octant_sort");
-    CK(cudaMemsetAsync(ws.counter.p, 0, sizeof(int), st), "memset");
-    if (!direct) CK(cudaMemsetAsync(out, 0, (size_t)out_rows * T * sizeof(int64_t), st), "memset");
+    KL(launch_fwd_prep(L.n, dirs, d, T, lo, hi, dflt ? 1 : 0, ws.M.p, ws.range.p, ws.beta.p, ws.perm.p, ws.octb.p,
+                       ws.counter.p, L.status, direct ? nullptr : reinterpret_cast<unsigned long long *>(out),
+                       out_rows * T, st),
+       "fwd_prep");
     CubicalFwdArgs a{};
     a.grids = L.d_grids;
     a.items = ws.items.p;
@@ -753,7 +754,7 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
         if ((s = upload_items(c->ws, items, st))) return s;
         c->ws.items_key = key;
     }
-    CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, c->L[0], c->climit, c->d_grid, &c->ws};
+    CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, c->L[0], c->climit, c->d_grid, &c->ws, c->d_status};
     return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st);
 }
 
@@ -823,8 +824,9 @@ extern "C" wect_status wect_compute(wect_complex c, const double *dirs, int d, i
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(c->mu);
+    if (c->kind == 0) return cubical_compute(c, dirs, d, T, lo, hi, out, st);   // directions checked in fwd_prep
     if ((s = dirs_check(c, dirs, d, st))) return s;
-    return c->kind == 0 ? cubical_compute(c, dirs, d, T, lo, hi, out, st) : simplicial_compute(c, dirs, d, T, lo, hi, out, st);
+    return simplicial_compute(c, dirs, d, T, lo, hi, out, st);
 }
 
 extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, double lo, double hi, int weighted,
@@ -1156,7 +1158,7 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
 static wect_status batch_enqueue(wect_batch b, const CubShape &sh, bool direct, const double *dirs, int d, int T,
                                  double lo, double hi, int64_t *out, cudaStream_t st)
 {
-    CubLaunch L{b->n, b->nsplit, b->wtype, b->frac_bits, b->kflush, b->maxL0, b->climit, b->d_grids, &b->ws};
+    CubLaunch L{b->n, b->nsplit, b->wtype, b->frac_bits, b->kflush, b->maxL0, b->climit, b->d_grids, &b->ws, b->d_status};
     return enqueue_cubical_fwd(L, sh, b->ws.n_items, direct, dirs, d, T, lo, hi, false, (int64_t)b->count * d, out, st);
 }
 

@@ -8,8 +8,9 @@ namespace wect {
 // Resolve the threshold range and fill beta (Section 3: beta(q) = q 2M/(T-1) - M, here for a
 // range [lo, hi]; the default range is [-M, M] with M the largest |height|).
 //   range[0] = lo, range[1] = hi, range[2] = step = (hi - lo)/(T - 1); beta[q] = lo + q*step.
-__global__ void setup_range_beta_kernel(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
-                                        double *range, double *beta)
+// Thread t of nt (over one or more blocks) fills its share.
+__device__ __forceinline__ void range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
+                                           double *range, double *beta, int t, int nt)
 {
     if (use_default) {
         const double M = __longlong_as_double((long long)*Mbits);
@@ -17,21 +18,28 @@ __global__ void setup_range_beta_kernel(double lo, double hi, int use_default, c
         hi = M;
     }
     const double step = __ddiv_rn(__dsub_rn(hi, lo), (double)(T - 1));
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (t == 0) {
         range[0] = lo;
         range[1] = hi;
         range[2] = step;
     }
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < T; q += gridDim.x * blockDim.x)
-        beta[q] = __dadd_rn(lo, __dmul_rn((double)q, step));
+    for (int q = t; q < T; q += nt) beta[q] = __dadd_rn(lo, __dmul_rn((double)q, step));
+}
+
+__global__ void setup_range_beta_kernel(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
+                                        double *range, double *beta)
+{
+    range_beta(lo, hi, use_default, Mbits, T, range, beta, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
 }
 
 // Grouping of the directions by octant (bit a set when s_a > 0): perm lists the directions
 // octant by octant, octb[o] is where octant o starts.  One block; the order inside an octant
 // is arbitrary (every consumer sums integers, so results do not depend on it).
-__global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, int *octb)
+// One block (any size); cnt/start/fill are shared arrays of the caller.
+__device__ __forceinline__ void octant_sort_block(int n, const double *dirs, int d, int *perm, int *octb, int *cnt,
+                                                  int *start, int *fill)
 {
-    __shared__ int cnt[8], start[9], fill[8];
     if (threadIdx.x < 8) {
         cnt[threadIdx.x] = 0;
         fill[threadIdx.x] = 0;
@@ -55,6 +63,43 @@ __global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, 
         for (int a = 0; a < n; ++a)
             if (dirs[(int64_t)p * n + a] > 0.0) o |= 1 << a;
         perm[start[o] + atomicAdd(&fill[o], 1)] = p;
+    }
+}
+
+__global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, int *octb)
+{
+    __shared__ int cnt[8], start[9], fill[8];
+    octant_sort_block(n, dirs, d, perm, octb, cnt, start, fill);
+}
+
+// Everything the cubical forward needs before its launch, in one kernel: block 0 checks the
+// directions for non-finite values (status flag), resolves the range and fills beta, groups the
+// directions by octant and clears the work-queue head; every block clears the output table
+// (when given) with 16-byte stores.
+__global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
+                                const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
+                                int *counter, int *status, unsigned long long *out, int64_t out_elems)
+{
+    if (blockIdx.x == 0) {
+        __shared__ int cnt[8], start[9], fill[8];
+        if (status)
+            for (int i = threadIdx.x; i < d * n; i += blockDim.x)
+                if (!isfinite(dirs[i])) atomicOr(status, kStatusBadIndex);
+        range_beta(lo, hi, use_default, Mbits, T, range, beta, threadIdx.x, blockDim.x);
+        octant_sort_block(n, dirs, d, perm, octb, cnt, start, fill);
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    if (out && out_elems > 0) {
+        // an 8-byte aligned table: one scalar head element when it is not 16-byte aligned
+        const int head = (reinterpret_cast<uintptr_t>(out) & 15u) ? 1 : 0;
+        ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(out + head);
+        const int64_t n2 = (out_elems - head) >> 1;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+            o2[i] = make_ulonglong2(0ull, 0ull);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (head) out[0] = 0ull;
+            if ((out_elems - head) & 1) out[out_elems - 1] = 0ull;
+        }
     }
 }
 
@@ -239,6 +284,18 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
                                     double *range, double *beta, cudaStream_t st)
 {
     setup_range_beta_kernel<<<grid_for(T, 256, 64), 256, 0, st>>>(lo, hi, use_default, Mbits, T, range, beta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
+                            const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
+                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st)
+{
+    if (out && (reinterpret_cast<uintptr_t>(out) & 7u)) return cudaErrorMisalignedAddress;   // int64 alignment
+    const int64_t work = out ? (out_elems / 2 + 255) / 256 : 1;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, 152 * 4));
+    fwd_prep_kernel<<<g, 256, 0, st>>>(n, dirs, d, T, lo, hi, use_default, Mbits, range, beta, perm, octb, counter,
+                                       status, out, out_elems);
     return cudaGetLastError();
 }
 

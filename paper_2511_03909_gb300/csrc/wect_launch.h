@@ -99,6 +99,11 @@ cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k
 cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,
                                     double *range, double *beta, cudaStream_t st);
 cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st);
+// Fused preparation of the cubical forward: direction check (status may be null), range and beta,
+// octant grouping, work-queue head, and (out non-null) a cleared output table of out_elems int64.
+cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
+                            const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
+                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st);
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
 cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
                                cudaStream_t st);

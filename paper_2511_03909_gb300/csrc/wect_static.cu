@@ -188,15 +188,14 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
         if (e_ != cudaSuccess) return sfail(WECT_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
     SCK(cudaMemsetAsync(S + kOffM, 0, 1024 - kOffM, st));     // max-|h| bits, queue head, status word
-    SCK(cudaMemsetAsync(out, 0, (size_t)d * T * sizeof(int64_t), st));
     static_setup_kernel<<<(ntiles * chunks + 255) / 256, 256, 0, st>>>(S, g, ntiles, chunks, per);
     SCK(cudaGetLastError());
-    note_launches(dflt ? 8 : 7);
+    note_launches(dflt ? 6 : 5);
     SCK(launch_weights_to_w32(wtype, vertex_weights, nv, 0, climit >> n, w32, status, st));
-    SCK(launch_finite_check(dirs, (int64_t)d * n, status, kStatusBadIndex, st));
     if (dflt) SCK(launch_grid_max_abs(n, grid, dirs, d, M, st));
-    SCK(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, M, T, range, beta, st));
-    SCK(launch_octant_sort(n, dirs, d, perm, octb, st));
+    // direction check, range and beta, octant grouping, queue head and a cleared output table
+    SCK(launch_fwd_prep(n, dirs, d, T, lo, hi, dflt ? 1 : 0, M, range, beta, perm, octb, counter, status,
+                        reinterpret_cast<unsigned long long *>(out), (int64_t)d * T, st));
     CubicalFwdArgs a{};
     a.grids = grid;
     a.items = items;

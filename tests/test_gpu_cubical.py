@@ -177,3 +177,20 @@ def test_argument_errors(P):
     assert ei.value.name == "INVALID_ARG"
     with pytest.raises(P.WectError):
         P.CubicalComplex(cuda(np.array([[np.inf, 1.0]], dtype=np.float32)), frac_bits=8)
+
+
+def test_output_table_with_8_byte_offset(P, O):
+    """An int64 output table that is 8- but not 16-byte aligned (a slice) is cleared and filled
+    exactly like an aligned one."""
+    dims = [21, 17, 5]
+    w = S.uniform_u8_grid(dims, seed=9)
+    dirs = S.fibonacci_directions(33)
+    cx = P.CubicalComplex(cuda(w))
+    T = 19
+    buf = torch.full((33 * T + 1,), 7, dtype=torch.int64, device="cuda")
+    out = buf[1:].view(33, T)
+    assert out.data_ptr() % 16 == 8
+    got = cx.wect(cuda(dirs), T, -SQ3, SQ3, out=out).cpu().numpy()
+    ref = O.wect_cubical(dims, w.ravel(), dirs, T, -SQ3, SQ3)
+    assert np.array_equal(got, ref)
+    assert int(buf[0]) == 7
