@@ -207,6 +207,12 @@ struct wect_complex_s {
     int64_t counts[4] = {0, 0, 0, 0};
     int32_t *d_simp[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t *d_sw[4] = {nullptr, nullptr, nullptr, nullptr};   // d_sw[0] = vertex weights (fixed)
+    // staged gather: per list of dim >= 1, chunk-local ids and per-chunk vertex lists
+    int2 *d_swp[4] = {nullptr, nullptr, nullptr, nullptr};    // packed signed weights of the gather
+    uint16_t *d_local[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *d_cverts[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *d_cnu[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t nchunks[4] = {0, 0, 0, 0};
     int sw_mode = WECT_SW_MAX_OF_VERTICES;
     // device state
     int *d_status = nullptr;
@@ -447,6 +453,8 @@ static wect_status upload_items(Workspace &ws, const std::vector<WorkItem> &item
 
 // ------------------------------------------------------------------ create / destroy
 
+static wect_status pack_simplicial_weights(wect_complex c, cudaStream_t st);
+
 static wect_status new_status_word(int **p)
 {
     CK(cudaMalloc((void **)p, sizeof(int)), "alloc");
@@ -656,6 +664,29 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
         const int64_t hb = (c->climit >> 16) + 1;
         c->kflush = (int)std::max<int64_t>(1, std::min<int64_t>(1 << 16, (((int64_t)1 << 31) - 1) / hb));
     }
+    // lists sorted by smallest vertex (results do not depend on the order; the gather's chunks
+    // then reference few distinct vertices)
+    for (int i = 1; i <= max_dim; ++i)
+        if (counts[i] > 1 && (e = sort_simplices_by_min_vertex(c->d_simp[i], counts[i], i + 1, c->d_sw[i], n_vertices, st)))
+            return cleanup(cuda_fail(e, "sort lists"));
+    for (int i = 0; i <= max_dim; ++i)
+        if ((e = cudaMalloc((void **)&c->d_swp[i], std::max<int64_t>(counts[i], 1) * sizeof(int2))))
+            return cleanup(cuda_fail(e, "alloc packed weights"));
+    if ((s = pack_simplicial_weights(c, st))) return cleanup(s);
+    // chunk-local ids of the lists of dim >= 1, for the staged gather (indices are valid here)
+    for (int i = 1; i <= max_dim; ++i) {
+        if (counts[i] == 0) continue;
+        const int m = i + 1;
+        const int64_t nch = (counts[i] + chunk_simplices(m) - 1) / chunk_simplices(m);
+        if ((e = cudaMalloc((void **)&c->d_local[i], (size_t)counts[i] * m * sizeof(uint16_t))) ||
+            (e = cudaMalloc((void **)&c->d_cverts[i], (size_t)nch * kWinRows * sizeof(int32_t))) ||
+            (e = cudaMalloc((void **)&c->d_cnu[i], (size_t)nch * sizeof(int32_t))))
+            return cleanup(cuda_fail(e, "alloc chunks"));
+        if ((e = launch_chunk_local(c->d_simp[i], counts[i], m, c->d_local[i], c->d_cverts[i], c->d_cnu[i], st)))
+            return cleanup(cuda_fail(e, "chunk_local"));
+        g_launches++;
+        c->nchunks[i] = nch;
+    }
     *out = c;
     return WECT_OK;
 }
@@ -670,6 +701,10 @@ extern "C" void wect_complex_destroy(wect_complex c)
     for (int i = 0; i < 4; ++i) {
         if (c->d_simp[i]) cudaFree(c->d_simp[i]);
         if (c->d_sw[i]) cudaFree(c->d_sw[i]);
+        if (c->d_swp[i]) cudaFree(c->d_swp[i]);
+        if (c->d_local[i]) cudaFree(c->d_local[i]);
+        if (c->d_cverts[i]) cudaFree(c->d_cverts[i]);
+        if (c->d_cnu[i]) cudaFree(c->d_cnu[i]);
     }
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_grid) cudaFree(c->d_grid);
@@ -722,6 +757,16 @@ extern "C" wect_status wect_complex_set_weights(wect_complex c, const void *w, w
     KL(launch_weights_check(WT_I64, c->d_sw[0], c->nv, 0, c->climit, c->d_status, st), "weights_check");
     for (int i = 1; i <= c->max_dim; ++i)
         if (c->counts[i] > 0) KL(launch_simplex_weights_max(c->d_simp[i], c->counts[i], i + 1, c->d_sw[0], c->d_sw[i], st), "sw");
+    return pack_simplicial_weights(c, st);
+}
+
+// Packed signed weights of every list (after the weights or the accumulator mode change).
+static wect_status pack_simplicial_weights(wect_complex c, cudaStream_t st)
+{
+    for (int i = 0; i <= c->max_dim; ++i) {
+        if (c->counts[i] == 0) continue;
+        KL(launch_pack_weights(c->d_sw[i], c->counts[i], (i & 1) ? -1 : 1, c->nsplit, c->d_swp[i], st), "pack_weights");
+    }
     return WECT_OK;
 }
 
@@ -786,16 +831,15 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
     if ((s = simplicial_range(c, dirs, d, T, lo, hi, st))) return s;
     CK(cudaMemsetAsync(out, 0, (size_t)d * T * sizeof(int64_t), st), "memset");
     const int grid = sm_count();
+    const bool staged_ok = simplex_fwd_staged_smem(c->nsplit, T, Dt) <= smem_optin() - 1024;
     ProfScope prof(st);
     for (int dt = 0; dt * Dt < d; ++dt) {
-        KL(launch_vertex_bins(c->n, c->d_coords, c->d_xf, c->nv, dirs, c->ws.dtab.p, d, dt, Dt, T, c->ws.beta.p, c->ws.bins.p,
-                              st),
-           "vertex_bins");
         for (int i = 0; i <= c->max_dim; ++i) {
-            if (c->counts[i] == 0) continue;
+            if (i > 0 && c->counts[i] == 0) continue;
             SimplexFwdArgs a{};
             a.simp = (i == 0) ? nullptr : c->d_simp[i];
             a.sw = c->d_sw[i];
+            a.swp = c->d_swp[i];
             a.k = c->counts[i];
             a.m = i + 1;
             a.sign = (i & 1) ? -1 : 1;
@@ -804,8 +848,29 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
             a.dtile = dt;
             a.d = d;
             a.T = T;
-            a.chunk = std::min<int64_t>(c->kflush, std::max<int64_t>(4096, (a.k + grid - 1) / grid));
+            // a multiple of 8 simplices, so that groups start on 16-byte boundaries
+            a.chunk = std::max<int64_t>(8, std::min<int64_t>(c->kflush, std::max<int64_t>(4096, (a.k + grid - 1) / grid)) & ~7ll);
             a.out = reinterpret_cast<unsigned long long *>(out);
+            if (i == 0) {
+                // vertex bins of the tile, fused with the vertices' own scatter (16 warps x 8
+                // vertices per CTA step)
+                a.flush_every = std::max(1, c->kflush / (16 * 8));
+                KL(launch_vertex_scatter(c->n, c->nsplit, a, c->d_coords, c->d_xf, c->nv, dirs, c->ws.dtab.p, c->ws.beta.p,
+                                         c->ws.bins.p, grid, st),
+                   "vertex_scatter");
+                continue;
+            }
+            const int cs = chunk_simplices(a.m);
+            if (i >= 1 && staged_ok && c->d_local[i] && c->kflush >= cs) {
+                a.local = c->d_local[i];
+                a.cverts = c->d_cverts[i];
+                a.cnu = c->d_cnu[i];
+                a.nchunks = c->nchunks[i];
+                a.flush_every = c->kflush / cs;           // at most kflush simplices between flushes
+                const int g = (int)std::min<int64_t>(grid, a.nchunks);
+                KL(launch_simplex_fwd_staged(c->nsplit, a, std::max(g, 1), st), "simplex_fwd_staged");
+                continue;
+            }
             const int g = (int)std::min<int64_t>(grid, (a.k + a.chunk - 1) / a.chunk);
             KL(launch_simplex_fwd(c->nsplit, a, std::max(g, 1), st), "simplex_fwd");
         }

@@ -50,6 +50,7 @@ struct CubicalBwdArgs {
 struct SimplexFwdArgs {
     const int32_t *simp;          // [k][m] vertex ids (m = dim + 1)
     const int64_t *sw;            // [k] fixed-point simplex weights
+    const int2 *swp;              // [k] packed signed weights (launch_pack_weights)
     int64_t k;
     int m;                        // vertices per simplex (1 = vertices themselves)
     int sign;                     // (-1)^dim
@@ -57,7 +58,28 @@ struct SimplexFwdArgs {
     int Dt, dtile, d, T;
     int64_t chunk;                // simplices per CTA work unit (<= flush bound)
     unsigned long long *out;      // [d][T] int64
+    // staged chunks (lists of dim >= 1, prepared at creation by launch_chunk_local)
+    const uint16_t *local;        // [k][m] chunk-local vertex ids
+    const int32_t *cverts;        // [nchunks][kWinRows] vertex ids of each chunk
+    const int32_t *cnu;           // [nchunks] distinct vertices of each chunk, -1 above kWinRows
+    int64_t nchunks;
+    int flush_every;              // chunks between histogram flushes
 };
+
+// Staged simplex chunks: kChunkSlots vertex slots per chunk (kChunkSlots / m simplices), and a
+// chunk is staged when it references at most kWinRows distinct vertices.
+constexpr int kChunkSlots = 1536;
+constexpr int kWinRows = 544;
+// Simplices per chunk: a multiple of 8 so that chunks and 8-simplex groups start on 16-byte
+// boundaries of the id and weight arrays.
+__host__ __device__ constexpr int chunk_simplices(int m) { return (kChunkSlots / m) & ~7; }
+// One shared-memory stage of the staged gather: the vertex-bin window (32 u16 per row), the
+// chunk-local ids and the packed weights of the chunk.
+constexpr int kWinBytes = kWinRows * 64;
+constexpr int kIdBytes = kChunkSlots * 2;
+constexpr int kWtBytes = chunk_simplices(2) * 8;
+constexpr int kStageBytes = kWinBytes + kIdBytes + kWtBytes;
+static_assert(kWinBytes % 16 == 0 && kIdBytes % 16 == 0 && kWtBytes % 16 == 0, "16-byte stage pieces");
 
 // cubical
 cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st);
@@ -82,6 +104,23 @@ cudaError_t launch_vertex_bins(int n, const double *coords, const float *xf, int
                                const float *tab, int d, int dtile, int Dt, int T, const double *beta, uint16_t *bins,
                                cudaStream_t st);
 cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st);
+// Vertex bins of a 32-direction tile fused with the vertices' own scatter (a: the list of dim 0).
+cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, const double *coords, const float *xf,
+                                  int64_t nv, const double *dirs, const float *tab, const double *beta, uint16_t *bins,
+                                  int grid, cudaStream_t st);
+// Packed signed weights for the gather: v = sign * sw; nsplit 1: {v, 0}, 2: {v & 0xFFFF, v >> 16}.
+cudaError_t launch_pack_weights(const int64_t *sw, int64_t k, int sign, int nsplit, int2 *out, cudaStream_t st);
+// Stable sort of a list of k simplices (m vertices each, in place) by smallest vertex id; sw (may
+// be null) is permuted alike.  Creation time only: it allocates and synchronises the stream.
+cudaError_t sort_simplices_by_min_vertex(int32_t *simp, int64_t k, int m, int64_t *sw, int64_t nv, cudaStream_t st);
+// Chunk-local ids of a list of k simplices with m vertices (m >= 2): per chunk its distinct vertices
+// (cverts, cnu) and the list rewritten in chunk-local 16-bit ids (local).
+cudaError_t launch_chunk_local(const int32_t *simp, int64_t k, int m, uint16_t *local, int32_t *cverts, int32_t *cnu,
+                               cudaStream_t st);
+// The staged gather (two shared-memory windows of kWinRows vertex rows next to the histogram);
+// returns cudaErrorInvalidValue when they do not fit.
+cudaError_t launch_simplex_fwd_staged(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st);
+size_t simplex_fwd_staged_smem(int nsplit, int T, int Dt);
 size_t simplex_fwd_smem(int nsplit, int T, int Dt);
 cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
                                       int d, unsigned long long *Mbits, float *Lscratch, cudaStream_t st);

@@ -6,6 +6,8 @@
 // the max of its vertex bins (equal to the bin of the max height, Eq. "msi") and adds the
 // signed simplex weight into a shared-memory histogram [T][Dt] (one column per lane, so a
 // red.shared of a warp hits 32 distinct banks), flushed into the int64 output.
+#include <climits>
+
 #include "wect_device.cuh"
 #include "wect_launch.h"
 
@@ -96,71 +98,419 @@ __global__ void __launch_bounds__(256) vertex_bins_kernel(const double *__restri
 
 // ------------------------------------------------------------------ simplex scatter
 
+// Loads from global memory (read-only path) or, with SMEM, from shared memory.
+template <bool SMEM, typename T>
+__device__ __forceinline__ T ld_ro(const T *p)
+{
+    if (SMEM) return *p;
+    return __ldg(p);
+}
+
+// One warp's share of GS consecutive simplices (n valid; n == GS when FULL) in a 32-direction
+// tile.  All vertex ids, packed signed weights and vertex bins of the group are loaded before any
+// is reduced, so GS dependent load chains are in flight.  Vertex ids are global int32 ids, chunk-
+// local uint16 ids, or for M == 1 the simplex index itself (vbase + g).  With SMEM the ids, the
+// weights and the bins (a window of chunk vertices) are in shared memory.  bins and histLane
+// already carry the lane's column; the max of the vertex bins (Eq. "msi") selects the histogram
+// row.
+template <int NSPLIT, int M, int GS, bool FULL, bool SMEM, typename IdT>
+__device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vbase, const int2 *__restrict__ wp, int n,
+                                             const uint16_t *__restrict__ bins, uint32_t histLane, uint32_t HOFF)
+{
+    int vid[GS][M];
+    int2 w[GS];
+    if (FULL) {
+        // a full group is GS consecutive simplices whose ids and weights start on 16-byte
+        // boundaries (chunks and groups are multiples of GS = 8 simplices): 128-bit loads
+        static_assert(GS == 8, "vector loads assume groups of 8");
+#pragma unroll
+        for (int q = 0; q < GS / 2; ++q) {
+            const int4 x = ld_ro<SMEM>(reinterpret_cast<const int4 *>(wp) + q);
+            w[2 * q] = make_int2(x.x, x.y);
+            w[2 * q + 1] = make_int2(x.z, x.w);
+        }
+        if (M == 1) {
+#pragma unroll
+            for (int g = 0; g < GS; ++g) vid[g][0] = vbase + g;
+        } else if (sizeof(IdT) == 2) {
+            uint32_t word[GS * M / 2];
+#pragma unroll
+            for (int q = 0; q < GS * M / 8; ++q) {
+                const uint4 x = ld_ro<SMEM>(reinterpret_cast<const uint4 *>(ids) + q);
+                word[4 * q] = x.x;
+                word[4 * q + 1] = x.y;
+                word[4 * q + 2] = x.z;
+                word[4 * q + 3] = x.w;
+            }
+#pragma unroll
+            for (int g = 0; g < GS; ++g)
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const int e = g * M + j;
+                    vid[g][j] = (int)((word[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+                }
+        } else {
+            int word[GS * M];
+#pragma unroll
+            for (int q = 0; q < GS * M / 4; ++q) {
+                const int4 x = ld_ro<SMEM>(reinterpret_cast<const int4 *>(ids) + q);
+                word[4 * q] = x.x;
+                word[4 * q + 1] = x.y;
+                word[4 * q + 2] = x.z;
+                word[4 * q + 3] = x.w;
+            }
+#pragma unroll
+            for (int g = 0; g < GS; ++g)
+#pragma unroll
+                for (int j = 0; j < M; ++j) vid[g][j] = word[g * M + j];
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < GS; ++g) {
+            const int gi = min(g, n - 1);
+#pragma unroll
+            for (int j = 0; j < M; ++j) vid[g][j] = (M == 1) ? vbase + gi : (int)ld_ro<SMEM>(ids + gi * M + j);
+            w[g] = (g < n) ? ld_ro<SMEM>(wp + gi) : make_int2(0, 0);
+        }
+    }
+    int bin[GS];
+#pragma unroll
+    for (int g = 0; g < GS; ++g) {
+        int bm = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            bm = max(bm, SMEM ? (int)bins[vid[g][j] * 32] : (int)__ldg(bins + (int64_t)vid[g][j] * 32));
+        bin[g] = bm;
+    }
+#pragma unroll
+    for (int g = 0; g < GS; ++g) {
+        const uint32_t addr = histLane + (uint32_t)bin[g] * 128u;
+        red_shared_add(addr, w[g].x);
+        if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+    }
+}
+
+// Add a CTA's [NSPLIT][T][32] int32 histogram (low 16 bits unsigned + high part when NSPLIT = 2)
+// into the int64 [d][T] difference table of the tile's directions, and clear it.
+template <int NSPLIT>
+__device__ __forceinline__ void simplex_flush(int32_t *hist, int T, int dtile, int d, unsigned long long *out)
+{
+    const int hw = T * 32;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
+        const int q = idx >> 5, c = idx & 31;
+        const int p = dtile * 32 + c;
+        int64_t v;
+        if (NSPLIT == 1) {
+            v = hist[idx];
+        } else {
+            v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
+            hist[hw + idx] = 0;
+        }
+        hist[idx] = 0;
+        if (p < d && v != 0) atomicAdd(out + (int64_t)p * T + q, (unsigned long long)v);
+    }
+    __syncthreads();
+}
+
+constexpr int kGatherGS = 8;
+
+// Gather for one 32-direction tile straight from the global bin table: CTAs take chunks of
+// P.chunk simplices (at most the flush bound), warps take groups of kGatherGS simplices.
 template <int NSPLIT, int M>
 __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const SimplexFwdArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int T = P.T, Dt = P.Dt;
-    const int hw = T * Dt;
+    constexpr int GS = kGatherGS;
+    const int T = P.T;
     int32_t *hist = reinterpret_cast<int32_t *>(smem);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t histAddr = smem_addr(hist);
-    const uint32_t HOFF = (uint32_t)hw * 4u;
-    for (int i = threadIdx.x; i < NSPLIT * hw; i += blockDim.x) hist[i] = 0;
+    const uint32_t histLane = smem_addr(hist) + (uint32_t)lane * 4u;
+    const uint32_t HOFF = (uint32_t)T * 128u;
+    for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
     __syncthreads();
+    const uint16_t *bins = P.bins + lane;
     const int64_t nchunks = (P.k + P.chunk - 1) / P.chunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int64_t b0 = ch * P.chunk, b1 = min(P.k, b0 + P.chunk);
-        // each warp takes GS simplices per step: their vertex ids, weights and vertex bins are all
-        // loaded before any is reduced, so GS dependent load chains are in flight per warp
-        constexpr int GS = 8;
         for (int64_t bb = b0 + (int64_t)wid * GS; bb < b1; bb += (int64_t)nw * GS) {
-            int vid[GS][M];
-            int64_t w[GS];
-#pragma unroll
-            for (int g = 0; g < GS; ++g) {
-                const int64_t b = min(bb + g, b1 - 1);
-#pragma unroll
-                for (int j = 0; j < M; ++j) vid[g][j] = (M == 1) ? (int)b : __ldg(P.simp + b * M + j);
-                w[g] = (bb + g < b1) ? __ldg(reinterpret_cast<const long long *>(P.sw) + b) : 0;
-            }
-            for (int c = lane; c < Dt; c += 32) {
-                int bin[GS];
-#pragma unroll
-                for (int g = 0; g < GS; ++g) {
-                    bin[g] = 0;
-#pragma unroll
-                    for (int j = 0; j < M; ++j) bin[g] = max(bin[g], (int)__ldg(P.bins + (int64_t)vid[g][j] * Dt + c));
-                }
-#pragma unroll
-                for (int g = 0; g < GS; ++g) {
-                    const int64_t sw = P.sign > 0 ? w[g] : -w[g];
-                    const uint32_t addr = histAddr + ((uint32_t)bin[g] * (uint32_t)Dt + (uint32_t)c) * 4u;
-                    if (NSPLIT == 1) {
-                        red_shared_add(addr, (int32_t)sw);
-                    } else {
-                        red_shared_add_u32(addr, (uint32_t)(sw & 0xFFFF));
-                        red_shared_add(addr + HOFF, (int32_t)(sw >> 16));
-                    }
-                }
-            }
+            const int n = (int)(b1 - bb < (int64_t)GS ? b1 - bb : (int64_t)GS);
+            const int32_t *ids = (M == 1) ? nullptr : P.simp + bb * M;
+            if (n == GS)
+                gather_group<NSPLIT, M, GS, true, false>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF);
+            else
+                gather_group<NSPLIT, M, GS, false, false>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF);
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
-            const int q = idx / Dt, c = idx - q * Dt;
-            const int p = P.dtile * Dt + c;
-            int64_t v;
-            if (NSPLIT == 1) {
-                v = hist[idx];
-            } else {
-                v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
-                hist[hw + idx] = 0;
-            }
-            hist[idx] = 0;
-            if (p < P.d && v != 0) atomicAdd(P.out + (int64_t)p * T + q, (unsigned long long)v);
-        }
-        __syncthreads();
+        simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
     }
+}
+
+// Packed signed weights of a list for the gather: v = (-1)^dim w; one plane: {v, 0}; two planes:
+// {low 16 bits of v, v >> 16}.
+__global__ void pack_weights_kernel(const int64_t *__restrict__ sw, int64_t k, int sign, int nsplit,
+                                    int2 *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = sign > 0 ? sw[i] : -sw[i];
+        out[i] = nsplit == 1 ? make_int2((int)v, 0) : make_int2((int)(v & 0xFFFF), (int)(v >> 16));
+    }
+}
+
+// The vertices' own scatter fused with their bins, for one 32-direction tile: each warp takes
+// VG consecutive vertices per step (lane = direction column), loads all their coordinates and
+// packed weights first, then computes each bin with the float32 filter (exact float64 path when
+// undecided), stores it for the simplices' gathers and adds the vertex weight into the CTA's
+// histogram.
+template <int N, int NSPLIT>
+__global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(const SimplexFwdArgs P,
+                                                                            const double *__restrict__ coords,
+                                                                            const float *__restrict__ xf, int64_t nv,
+                                                                            const double *__restrict__ dirs,
+                                                                            const float *__restrict__ tab,
+                                                                            const double *__restrict__ beta,
+                                                                            uint16_t *__restrict__ bins)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int VG = 8;
+    const int T = P.T, d = P.d;
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t histLane = smem_addr(hist) + (uint32_t)lane * 4u;
+    const uint32_t HOFF = (uint32_t)T * 128u;
+    for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const int p = P.dtile * 32 + lane;
+    const bool act = p < d;
+    const int pc = act ? p : d - 1;
+    const float4 t0 = __ldg(reinterpret_cast<const float4 *>(tab + (int64_t)pc * 8));
+    const float eta = __ldg(tab + (int64_t)pc * 8 + 4);
+    const float Af[3] = {t0.x, t0.y, t0.z};
+    // CTA-uniform steps of nw * VG vertices (so that the periodic flush is a block-wide barrier),
+    // at most P.flush_every steps between flushes
+    const int64_t cstep = (int64_t)nw * VG;
+    int since = 0;
+    for (int64_t base = (int64_t)blockIdx.x * cstep; base < nv; base += (int64_t)gridDim.x * cstep) {
+        const int64_t v0 = base + (int64_t)wid * VG;
+        float x[VG][3];
+        int2 w[VG];
+#pragma unroll
+        for (int g = 0; g < VG; ++g) {
+            const int64_t v = min(v0 + g, nv - 1);
+#pragma unroll
+            for (int a = 0; a < N; ++a) x[g][a] = __ldg(xf + v * N + a);
+            w[g] = (v0 + g < nv) ? __ldg(P.swp + v) : make_int2(0, 0);
+        }
+#pragma unroll
+        for (int g = 0; g < VG; ++g) {
+            const int64_t v = min(v0 + g, nv - 1);
+            float u = t0.w;
+#pragma unroll
+            for (int a = N - 1; a >= 0; --a) u = __fmaf_rn(x[g][a], Af[a], u);
+            const int tlo = __float_as_int(__fadd_ru(__fsub_rd(u, eta), kMagic));
+            const int thi = __float_as_int(__fadd_ru(__fadd_ru(u, eta), kMagic));
+            int b = clamp_bin(thi, 0, T);
+            if (tlo != thi) {
+                double xd[3] = {0.0, 0.0, 0.0};
+                for (int a = 0; a < N; ++a) xd[a] = coords[v * N + a];
+                const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
+                b = exact_bin_from(h, beta, T, b);
+            }
+            if (act && v0 + g < nv) bins[v * 32 + lane] = (uint16_t)b;
+            const uint32_t addr = histLane + (uint32_t)b * 128u;
+            red_shared_add(addr, w[g].x);
+            if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+        }
+        if (++since >= P.flush_every) {
+            simplex_flush<NSPLIT>(hist, T, P.dtile, d, P.out);
+            since = 0;
+        }
+    }
+    if (since > 0) simplex_flush<NSPLIT>(hist, T, P.dtile, d, P.out);
+}
+
+// ------------------------------------------------------------------ staged chunks
+
+// Creation-time pass over a list of simplices with M >= 2 vertices, one CTA per chunk of
+// chunk_simplices(M) simplices: sort the chunk's vertex ids, keep the distinct ones (thread 0, a
+// serial pass over at most kChunkSlots sorted ids), and when there are at most kWinRows of them
+// store them in cverts and rewrite the chunk's ids as their ranks (16 bits).  cnu is the number
+// of distinct vertices, or -1 for a chunk the gather reads straight from global memory.
+template <int M>
+__global__ void __launch_bounds__(512) chunk_local_kernel(const int32_t *__restrict__ simp, int64_t k,
+                                                          uint16_t *__restrict__ local, int32_t *__restrict__ cverts,
+                                                          int32_t *__restrict__ cnu)
+{
+    constexpr int C = chunk_simplices(M);
+    constexpr int NK = 2048;              // power of two >= kChunkSlots
+    __shared__ int keys[NK];
+    __shared__ int U;
+    const int64_t s0 = (int64_t)blockIdx.x * C;
+    const int nslot = (int)(k - s0 < (int64_t)C ? k - s0 : (int64_t)C) * M;
+    for (int j = threadIdx.x; j < NK; j += blockDim.x) keys[j] = (j < nslot) ? simp[s0 * M + j] : INT_MAX;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int size = 2; size <= NK; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int j = threadIdx.x; j < NK / 2; j += blockDim.x) {
+                const int lo = 2 * j - (j & (stride - 1)), hi = lo + stride;
+                const int a = keys[lo], b = keys[hi];
+                if ((a > b) == ((lo & size) == 0)) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        int u = 0;
+        for (int j = 0; j < nslot; ++j)
+            if (j == 0 || keys[j] != keys[j - 1]) keys[u++] = keys[j];
+        U = u;
+        cnu[blockIdx.x] = (u <= kWinRows) ? u : -1;
+    }
+    __syncthreads();
+    const int u = U;
+    if (u > kWinRows) return;
+    for (int j = threadIdx.x; j < u; j += blockDim.x) cverts[(int64_t)blockIdx.x * kWinRows + j] = keys[j];
+    for (int j = threadIdx.x; j < nslot; j += blockDim.x) {
+        const int v = simp[s0 * M + j];
+        int lo = 0, hi = u - 1;                 // keys[0..u) is sorted and holds v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        local[s0 * M + j] = (uint16_t)lo;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// 16-byte copy of which only the first n bytes come from src (the rest is zero-filled).
+__device__ __forceinline__ void cp_async16_n(uint32_t dst, const void *src, int n)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Staged gather for lists of dim >= 1 (M >= 2 vertices per simplex), one 32-direction tile.  Each
+// CTA walks a contiguous range of chunks.  For a staged chunk, cp.async copies its vertex-bin rows
+// (64 bytes each, a window of at most kWinRows chunk vertices), its chunk-local ids and its packed
+// weights into one of two shared-memory buffers while the previous chunk is reduced, so every
+// load of the reduction is a shared-memory load.  Chunks with more than kWinRows distinct
+// vertices read global memory as simplex_fwd_kernel does.  The histogram and flush are those of
+// simplex_fwd_kernel.
+template <int NSPLIT, int M>
+__global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(const SimplexFwdArgs P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int C = chunk_simplices(M);
+    constexpr int GS = kGatherGS;
+    constexpr int NWIN = 4 * kWinRows;                           // 16-byte pieces of a full window
+    constexpr int NID = (C * M * 2 + 15) / 16;                    // ... of the chunk's ids
+    constexpr int NWT = (C * 8 + 15) / 16;                        // ... of its weights
+    constexpr int NCP = (NWIN + NID + NWT + kSimplexThreads - 1) / kSimplexThreads;
+    const int T = P.T;
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);
+    const size_t hbytes = ((size_t)NSPLIT * T * 128u + 15u) & ~(size_t)15u;
+    const uint32_t histAddr = smem_addr(hist);
+    unsigned char *bufBase = smem + hbytes;
+    const uint32_t bufAddr = histAddr + (uint32_t)hbytes;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const uint32_t histLane = histAddr + (uint32_t)lane * 4u;
+    const uint32_t HOFF = (uint32_t)T * 128u;
+    for (int i = tid; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
+    const int64_t cb = P.nchunks * blockIdx.x / gridDim.x, ce = P.nchunks * (blockIdx.x + 1) / gridDim.x;
+
+    // window rows of this thread's copies of chunk c (vertex id, or -1) and the chunk's width u
+    auto load_vids = [&](int64_t c, int *v, int &u) {
+        u = (c < ce) ? __ldg(P.cnu + c) : -1;
+#pragma unroll
+        for (int i = 0; i < NCP; ++i) {
+            const int q = tid + i * kSimplexThreads;
+            v[i] = (q < 4 * u) ? __ldg(P.cverts + c * kWinRows + (q >> 2)) : -1;
+        }
+    };
+    // cp.async of chunk c into buffer buf: 4u window pieces, then ids, then weights (the last
+    // pieces of the lists are zero-filled beyond their ends)
+    auto issue = [&](int buf, int64_t c, const int *v, int u) {
+        if (u >= 0) {
+            const int64_t s0 = c * C;
+            const int ns = (int)(P.k - s0 < (int64_t)C ? P.k - s0 : (int64_t)C);
+            const int idb = ns * M * 2, wtb = ns * 8;
+            const int nid = (idb + 15) / 16, nwt = (wtb + 15) / 16;
+            const uint32_t b0 = bufAddr + (uint32_t)buf * kStageBytes;
+            const unsigned char *ids = reinterpret_cast<const unsigned char *>(P.local + s0 * M);
+            const unsigned char *wts = reinterpret_cast<const unsigned char *>(P.swp + s0);
+#pragma unroll
+            for (int i = 0; i < NCP; ++i) {
+                const int q = tid + i * kSimplexThreads;
+                if (q < 4 * u) {
+                    cp_async16(b0 + (uint32_t)q * 16u, P.bins + (int64_t)v[i] * 32 + (q & 3) * 8);
+                } else if (q < 4 * u + nid) {
+                    const int r = q - 4 * u;
+                    cp_async16_n(b0 + kWinBytes + (uint32_t)r * 16u, ids + r * 16, min(16, idb - r * 16));
+                } else if (q < 4 * u + nid + nwt) {
+                    const int r = q - 4 * u - nid;
+                    cp_async16_n(b0 + kWinBytes + kIdBytes + (uint32_t)r * 16u, wts + r * 16, min(16, wtb - r * 16));
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    int vA[NCP], vB[NCP], uA, uB;
+    load_vids(cb, vA, uA);
+    issue(0, cb, vA, uA);
+    load_vids(cb + 1, vB, uB);
+    int since = 0, u = uA;
+    for (int64_t c = cb; c < ce; ++c) {
+        const int buf = (int)((c - cb) & 1);
+        issue(buf ^ 1, c + 1, vB, uB);          // chunk c + 1 (nothing when past the range)
+        const int unext = uB;
+        load_vids(c + 2, vB, uB);               // consumed by the next iteration's issue
+        cp_async_wait<1>();                     // this thread's copies of chunk c are done
+        __syncthreads();                        // and everyone's (and the histogram is cleared)
+        const int64_t s0 = c * C;
+        const int ns = (int)(P.k - s0 < (int64_t)C ? P.k - s0 : (int64_t)C);
+        if (u >= 0) {
+            const unsigned char *bb0 = bufBase + (size_t)buf * kStageBytes;
+            const uint16_t *wb = reinterpret_cast<const uint16_t *>(bb0) + lane;
+            const uint16_t *sid = reinterpret_cast<const uint16_t *>(bb0 + kWinBytes);
+            const int2 *swt = reinterpret_cast<const int2 *>(bb0 + kWinBytes + kIdBytes);
+            for (int bb = wid * GS; bb < ns; bb += nw * GS) {
+                const int n = min(GS, ns - bb);
+                if (n == GS)
+                    gather_group<NSPLIT, M, GS, true, true>(sid + bb * M, 0, swt + bb, n, wb, histLane, HOFF);
+                else
+                    gather_group<NSPLIT, M, GS, false, true>(sid + bb * M, 0, swt + bb, n, wb, histLane, HOFF);
+            }
+        } else {
+            const uint16_t *gb = P.bins + lane;
+            for (int bb = wid * GS; bb < ns; bb += nw * GS) {
+                const int n = min(GS, ns - bb);
+                const int32_t *ids = P.simp + (s0 + bb) * M;
+                if (n == GS)
+                    gather_group<NSPLIT, M, GS, true, false>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
+                else
+                    gather_group<NSPLIT, M, GS, false, false>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
+            }
+        }
+        __syncthreads();                        // buffer buf is free for chunk c + 2
+        if (++since >= P.flush_every) {
+            simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
+            since = 0;
+        }
+        u = unext;
+    }
+    cp_async_wait<0>();
+    if (since > 0) simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
 }
 
 // ------------------------------------------------------------------ default range
@@ -321,6 +671,29 @@ cudaError_t launch_vertex_bins(int n, const double *coords, const float *xf, int
     return cudaGetLastError();
 }
 
+cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, const double *coords, const float *xf,
+                                  int64_t nv, const double *dirs, const float *tab, const double *beta, uint16_t *bins,
+                                  int grid, cudaStream_t st)
+{
+    if (a.Dt != 32 || !a.swp) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)nsplit * a.T * 128u;
+    cudaError_t e = cudaSuccess;
+#define VS(NN, SS)                                                                                                   \
+    do {                                                                                                             \
+        e = cudaFuncSetAttribute(vertex_scatter_kernel<NN, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e == cudaSuccess)                                                                                        \
+            vertex_scatter_kernel<NN, SS><<<grid, kSimplexThreads, sm, st>>>(a, coords, xf, nv, dirs, tab, beta, bins); \
+    } while (0)
+    if (nsplit == 1) {
+        if (n == 1) VS(1, 1); else if (n == 2) VS(2, 1); else VS(3, 1);
+    } else {
+        if (n == 1) VS(1, 2); else if (n == 2) VS(2, 2); else VS(3, 2);
+    }
+#undef VS
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 size_t simplex_fwd_smem(int nsplit, int T, int Dt) { return (size_t)nsplit * T * Dt * 4u; }
 
 template <int NSPLIT>
@@ -347,7 +720,60 @@ static cudaError_t launch_simplex_fwd_s(const SimplexFwdArgs &a, int grid, cudaS
 
 cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st)
 {
+    if (a.Dt != 32 || !a.swp) return cudaErrorInvalidValue;
     return nsplit == 1 ? launch_simplex_fwd_s<1>(a, grid, st) : launch_simplex_fwd_s<2>(a, grid, st);
+}
+
+cudaError_t launch_pack_weights(const int64_t *sw, int64_t k, int sign, int nsplit, int2 *out, cudaStream_t st)
+{
+    if (k <= 0) return cudaSuccess;
+    pack_weights_kernel<<<(unsigned)std::min<int64_t>((k + 255) / 256, 152 * 16), 256, 0, st>>>(sw, k, sign, nsplit, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_local(const int32_t *simp, int64_t k, int m, uint16_t *local, int32_t *cverts, int32_t *cnu,
+                               cudaStream_t st)
+{
+    if (k <= 0 || m < 2) return cudaSuccess;
+    const int64_t nch = (k + chunk_simplices(m) - 1) / chunk_simplices(m);
+    switch (m) {
+    case 2: chunk_local_kernel<2><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
+    case 3: chunk_local_kernel<3><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
+    default: chunk_local_kernel<4><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
+    }
+    return cudaGetLastError();
+}
+
+size_t simplex_fwd_staged_smem(int nsplit, int T, int Dt)
+{
+    return (((size_t)nsplit * T * Dt * 4u + 15u) & ~(size_t)15u) + 2u * kStageBytes;
+}
+
+template <int NSPLIT>
+static cudaError_t launch_simplex_fwd_staged_s(const SimplexFwdArgs &a, int grid, cudaStream_t st)
+{
+    const size_t sm = simplex_fwd_staged_smem(NSPLIT, a.T, a.Dt);
+    cudaError_t e = cudaSuccess;
+#define SS(MM)                                                                                                        \
+    do {                                                                                                              \
+        e = cudaFuncSetAttribute(simplex_fwd_staged_kernel<NSPLIT, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)sm);                                                                            \
+        if (e == cudaSuccess) simplex_fwd_staged_kernel<NSPLIT, MM><<<grid, kSimplexThreads, sm, st>>>(a);           \
+    } while (0)
+    switch (a.m) {
+    case 2: SS(2); break;
+    case 3: SS(3); break;
+    default: SS(4); break;
+    }
+#undef SS
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_simplex_fwd_staged(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st)
+{
+    if (a.Dt != 32 || a.m < 2 || a.m > 4 || !a.swp) return cudaErrorInvalidValue;
+    return nsplit == 1 ? launch_simplex_fwd_staged_s<1>(a, grid, st) : launch_simplex_fwd_staged_s<2>(a, grid, st);
 }
 
 cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,

@@ -124,3 +124,24 @@ def test_bad_indices_rejected(P):
     cx2 = S.Simplicial(coords=X2, simplices=[E[:1]], weights=np.ones(4, np.uint8))
     with pytest.raises(P.WectError):
         _make(P, cx2, cx2.weights)
+
+
+def test_staged_and_direct_chunks(P, oracle):
+    """Lists are cut into chunks. A chunk that references at most a shared-memory window of
+    distinct vertices is staged through shared memory; a larger one reads global memory. The
+    complexes here mix both kinds: a 160^2 mesh whose triangle list is shuffled in its second
+    half, and a random complex on 20000 vertices, where every chunk reads global memory."""
+    cx = S.jittered_grid_mesh(160, seed=11)
+    tri = cx.simplices[1].copy()
+    half = len(tri) // 2
+    tri[half:] = tri[half:][np.random.default_rng(12).permutation(len(tri) - half)]
+    mixed = S.Simplicial(cx.coords, [cx.simplices[0], tri], cx.weights)
+    rnd = S.random_simplicial(20000, 2, 6000, 4000, seed=13)
+    dirs = S.circle_directions(40)
+    for c, fb, rng_ in ((mixed, 24, (-1.5, 1.5)), (mixed, 24, (math.nan, math.nan)), (rnd, 0, (-1.2, 1.3))):
+        h = _make(P, c, c.weights, fb=fb)
+        got = h.wect(cuda(dirs), 64, *rng_).cpu().numpy()
+        vw = oracle.fixed_from_f32(c.weights, fb) if fb else c.weights.astype(np.int64)
+        ref = oracle.wect_simplicial(c.coords, c.simplices, oracle.simplicial_weights(c.simplices, vw), dirs, 64, *rng_)
+        assert np.array_equal(got, ref)
+        h.device_status()
