@@ -210,6 +210,38 @@ def closure_from_top(coords: np.ndarray, top: np.ndarray) -> Simplicial:
     return Simplicial(coords=np.ascontiguousarray(coords), simplices=lists, weights=np.ones(coords.shape[0], dtype=np.uint8))
 
 
+def tetra_grid(side: int, seed: int, jitter: float = 0.2) -> Simplicial:
+    """Solid side^3 jittered grid in [-1,1]^3 cut into tetrahedra (six per cube cell, one per
+    ordering of the axes: the path lower corner -> +e_a -> +e_a+e_b -> upper corner), with all
+    their faces.  A triangulated solid cube: Euler characteristic 1.  u8 weights."""
+    rng = np.random.default_rng(seed)
+    L = side
+    h = 2.0 / (L - 1)
+    g = -1.0 + 2.0 * np.arange(L, dtype=np.float64) / (L - 1)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    coords = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    coords = coords + rng.uniform(-jitter * h, jitter * h, size=coords.shape)
+    from itertools import permutations
+
+    def vid(x, y, z):
+        return (z * L + y) * L + x
+
+    tets = []
+    for z in range(L - 1):
+        for y in range(L - 1):
+            for x in range(L - 1):
+                for perm in permutations(range(3)):
+                    p = [x, y, z]
+                    path = [vid(*p)]
+                    for a in perm:
+                        p[a] += 1
+                        path.append(vid(*p))
+                    tets.append(path)
+    cx = closure_from_top(coords, np.array(tets, dtype=np.int64))
+    cx.weights = rng.integers(0, 256, size=coords.shape[0], dtype=np.uint8)
+    return cx
+
+
 def random_simplicial(nv: int, n: int, k1: int, k2: int, seed: int, coord_bits: int | None = None) -> Simplicial:
     """Random (not necessarily closed) complex: nv random points, k1 random edges, k2 random
     triangles, u8 weights.  With coord_bits, coordinates are multiples of 2^-coord_bits in

@@ -145,3 +145,21 @@ def test_staged_and_direct_chunks(P, oracle):
         ref = oracle.wect_simplicial(c.coords, c.simplices, oracle.simplicial_weights(c.simplices, vw), dirs, 64, *rng_)
         assert np.array_equal(got, ref)
         h.device_status()
+
+
+def test_tetrahedral_grid_forward_and_adjoint(P, oracle):
+    """A 12^3 solid cube cut into tetrahedra (lists of dim 1, 2 and 3), u8 weights: the forward
+    with the default and a fixed range, and the adjoint, against the oracle."""
+    cx = S.tetra_grid(12, seed=22)
+    dirs = S.fibonacci_directions(70)
+    vw = cx.weights.astype(np.int64)
+    h = _make(P, cx, cx.weights)
+    for T, lo, hi in ((64, math.nan, math.nan), (97, -1.5, 1.6)):
+        got = h.wect(cuda(dirs), T, lo, hi).cpu().numpy()
+        ref = oracle.wect_simplicial(cx.coords, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), dirs, T, lo, hi)
+        assert np.array_equal(got, ref)
+    G = np.random.default_rng(23).integers(-5000, 5000, (len(dirs), 40)).astype(np.int64)
+    g = h.backward(cuda(dirs), 40, -1.5, 1.6, cuda(G), 0.5).cpu().numpy()
+    ref = oracle.wect_backward_simplicial(cx.coords, vw, cx.simplices, dirs, 40, -1.5, 1.6, G, 0.5)
+    assert np.array_equal(g, ref)
+    h.device_status()

@@ -341,6 +341,26 @@ def test_brute_force_simplicial_rounding(oracle):
             assert got[p].tolist() == brute_wecf(cx.nv, faces, weights, f, T, beta)
 
 
+def test_tetrahedral_solid_cube(oracle):
+    """Lists with tetrahedra: a triangulated solid cube (six tetrahedra per cell) has Euler
+    characteristic 1, and brute-force enumeration of its sublevel subcomplexes (float64
+    heights from the exact-fma restatement) equals the oracle, weights included."""
+    cx = S.tetra_grid(3, seed=21)
+    one = oracle.simplicial_weights(cx.simplices, np.ones(cx.nv, dtype=np.int64), "one")
+    dirs = S.fibonacci_directions(6)
+    W = oracle.wect_simplicial(cx.coords, cx.simplices, one, dirs, 11)
+    assert np.all(W[:, -1] == 1)
+    vw = cx.weights.astype(np.int64)
+    T, lo, hi = 13, -1.6, 1.7
+    got = oracle.wect_simplicial(cx.coords, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), dirs, T, lo, hi)
+    faces, weights = simplicial_faces(cx, vw)
+    step = (hi - lo) / (T - 1)
+    beta = [lo + q * step for q in range(T)]
+    for p in range(len(dirs)):
+        f = [height_reading(list(cx.coords[v]), list(dirs[p])) for v in range(cx.nv)]
+        assert got[p].tolist() == brute_wecf(cx.nv, faces, weights, f, T, beta)
+
+
 @pytest.mark.parametrize("dims", [[5], [4, 3], [3, 2, 3], [2, 2, 2]])
 def test_brute_force_cubical(oracle, dims):
     rng = np.random.default_rng(sum(dims))
