@@ -161,6 +161,21 @@ WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, in
 WECT_API wect_status ecf_compute(wect_complex cx, const double *filter, int T, double lo, double hi, int weighted,
                         int64_t *out, wect_stream stream);
 
+/*
+ * The WECF table of m caller-supplied vertex filters (Algorithm 1 with m filters, Section 3):
+ *   out[p][q] = sum over cells s with bin(max_{v in s} f_p(v)) <= q of (-1)^dim(s) w(s),
+ * with the same thresholds and bins as wect_compute.  Both lo and hi NaN select [-M, M] with M
+ * the largest |f_p(v)| over all m filters, as in the paper.  ecf_compute is the case m = 1.
+ *   filters (dev) [m][k_0] float64, finite (a non-finite value sets the status word)
+ *   m             number of filters, 1..65535
+ *   weighted      0 => every cell has weight 1; otherwise the complex's weights
+ *   out (dev)     [m][T] int64
+ * Errors: INVALID_ARG for NULL pointers, m out of range or a bad range; UNSUPPORTED for
+ * T > 65535.  Workspace: m * k_0 uint16 bins, grown on demand and kept with the complex.
+ */
+WECT_API wect_status wecf_compute(wect_complex cx, const double *filters, int m, int T, double lo, double hi,
+                         int weighted, int64_t *out, wect_stream stream);
+
 /* ---------------------------------------------------------------- adjoint */
 
 /*

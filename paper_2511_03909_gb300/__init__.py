@@ -75,6 +75,7 @@ def _declare(L):
         "wect_complex_destroy": (None, [_p]),
         "wect_compute": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
         "ecf_compute": (_st, [_p, _p, _i, _d, _d, _i, _p, _p]),
+        "wecf_compute": (_st, [_p, _p, _i, _i, _d, _d, _i, _p, _p]),
         "wect_backward": (_st, [_p, _p, _i, _i, _d, _d, _p, _d, _p, _p]),
         "wect_batch_create": (_st, [_i, _p, _p]),
         "wect_batch_create_cubical": (_st, [_i, _i, _p, _p, _i, _i, _p, _p]),
@@ -105,7 +106,7 @@ def exported_symbols():
     return [
         "wect_complex_create_cubical", "wect_complex_create_simplicial", "wect_complex_set_weights",
         "wect_complex_num_vertices", "wect_complex_cell_counts", "wect_complex_device_status",
-        "wect_complex_destroy", "wect_compute", "ecf_compute", "wect_backward", "wect_batch_create",
+        "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
         "wect_batch_autotune",
@@ -218,6 +219,19 @@ class _Complex:
         if out is None:
             out = torch.empty(T, dtype=torch.int64, device=filt.device)
         _check(load().ecf_compute(self._h, _ptr(filt), T, lo, hi, int(weighted), _ptr(out), _stream()))
+        return out
+
+    def wecf(self, filters: torch.Tensor, T: int, lo: float = math.nan, hi: float = math.nan,
+             weighted: bool = True, out: torch.Tensor | None = None) -> torch.Tensor:
+        """[m][T] int64 WECF table of m vertex filters given as [m][nv] float64 (wecf_compute)."""
+        _require_cuda(filters, "filters", torch.float64)
+        if filters.dim() != 2 or filters.shape[1] != self.nv:
+            raise ValueError("filters must be [m][nv]")
+        m = filters.shape[0]
+        if out is None:
+            out = torch.empty((m, T), dtype=torch.int64, device=filters.device)
+        _require_cuda(out, "out", torch.int64)
+        _check(load().wecf_compute(self._h, _ptr(filters), m, T, lo, hi, int(weighted), _ptr(out), _stream()))
         return out
 
     def backward(self, dirs: torch.Tensor, T: int, lo: float, hi: float, dW: torch.Tensor, scale: float,

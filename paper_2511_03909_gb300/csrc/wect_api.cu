@@ -894,40 +894,57 @@ extern "C" wect_status wect_compute(wect_complex c, const double *dirs, int d, i
     return simplicial_compute(c, dirs, d, T, lo, hi, out, st);
 }
 
-extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, double lo, double hi, int weighted,
-                                   int64_t *out, wect_stream stream)
+// Algorithm 1 for m caller-supplied vertex filters [m][nv]: exact float64 bins of every filter,
+// then the per-cell max of the bins and the signed scatter, one histogram row per filter.
+static wect_status wecf_impl(wect_complex c, const double *filters, int m, int T, double lo, double hi, int weighted,
+                             int64_t *out, cudaStream_t st)
 {
     if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
-    if (!filter || !out) return fail(WECT_ERR_INVALID_ARG, "filter/out is NULL");
+    if (!filters || !out) return fail(WECT_ERR_INVALID_ARG, "filters/out is NULL");
+    if (m < 1 || m > 65535) return fail(WECT_ERR_INVALID_ARG, "m must be in [1, 65535] (got %d)", m);
     wect_status s = check_range(lo, hi, T);
     if (s) return s;
-    cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(c->mu);
     if ((s = ensure_common_ws(c->ws, T))) return s;
-    CK(c->ws.bins.ensure((size_t)c->nv), "alloc bins");
-    KL(launch_finite_check(filter, c->nv, c->d_status, kStatusBadIndex, st), "finite_check");
+    const int64_t total = (int64_t)m * c->nv;
+    CK(c->ws.bins.ensure((size_t)total), "alloc bins");
+    KL(launch_finite_check(filters, total, c->d_status, kStatusBadIndex, st), "finite_check");
     const bool dflt = range_is_default(lo, hi);
     if (dflt) {
+        // the paper's M is the largest |f| over all m filters
         CK(cudaMemsetAsync(c->ws.M.p, 0, sizeof(unsigned long long), st), "memset");
-        KL(launch_max_abs_f64(filter, c->nv, 1, 0, c->ws.M.p, st), "max_abs");
+        KL(launch_max_abs_f64(filters, total, 1, 0, c->ws.M.p, st), "max_abs");
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
-    KL(launch_filter_bins(filter, c->nv, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, st), "filter_bins");
-    CK(cudaMemsetAsync(out, 0, (size_t)T * sizeof(int64_t), st), "memset");
+    KL(launch_filter_bins(filters, total, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, st), "filter_bins");
+    CK(cudaMemsetAsync(out, 0, (size_t)m * T * sizeof(int64_t), st), "memset");
     if (c->kind == 0) {
         KL(launch_cubical_ecf(c->n, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0,
-                              reinterpret_cast<unsigned long long *>(out), c->nv, st),
+                              reinterpret_cast<unsigned long long *>(out), c->nv, m, st),
            "cubical_ecf");
     } else {
         for (int i = 0; i <= c->max_dim; ++i) {
             if (c->counts[i] == 0) continue;
             KL(launch_simplex_ecf(i == 0 ? nullptr : c->d_simp[i], c->d_sw[i], c->counts[i], i + 1, (i & 1) ? -1 : 1,
-                                  weighted ? 1 : 0, c->ws.bins.p, T, reinterpret_cast<unsigned long long *>(out), st),
+                                  weighted ? 1 : 0, c->ws.bins.p, T, reinterpret_cast<unsigned long long *>(out), c->nv,
+                                  m, st),
                "simplex_ecf");
         }
     }
-    KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), 1, T, st), "scan_rows");
+    KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), m, T, st), "scan_rows");
     return WECT_OK;
+}
+
+extern "C" wect_status ecf_compute(wect_complex c, const double *filter, int T, double lo, double hi, int weighted,
+                                   int64_t *out, wect_stream stream)
+{
+    return wecf_impl(c, filter, 1, T, lo, hi, weighted, out, (cudaStream_t)stream);
+}
+
+extern "C" wect_status wecf_compute(wect_complex c, const double *filters, int m, int T, double lo, double hi,
+                                    int weighted, int64_t *out, wect_stream stream)
+{
+    return wecf_impl(c, filters, m, T, lo, hi, weighted, out, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ adjoint

@@ -451,6 +451,8 @@ __global__ void __launch_bounds__(256) cubical_ecf_kernel(const GridDesc *grids,
     for (int i = threadIdx.x; i < T; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const GridDesc g = grids[0];
+    bins += (int64_t)blockIdx.y * g.nv;     // filter blockIdx.y of [m][nv] bins, row of [m][T] out
+    out += (int64_t)blockIdx.y * T;
     const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.nv; v += (int64_t)gridDim.x * blockDim.x) {
         const int i0 = (int)(v % L0), i1 = (int)((v / L0) % L1), i2 = (int)(v / ((int64_t)L0 * L1));
@@ -559,9 +561,9 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0)
 int cubical_fwd_threads() { return kFwdThreads; }
 
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
-                               unsigned long long *out, int64_t nv, cudaStream_t st)
+                               unsigned long long *out, int64_t nv, int nf, cudaStream_t st)
 {
-    const int blocks = (int)std::min<int64_t>((nv + 255) / 256, 1024);
+    const dim3 blocks((unsigned)std::min<int64_t>((nv + 255) / 256, std::max(8, 1024 / std::max(nf, 1))), (unsigned)nf);
     const size_t sm = (size_t)T * 8u;
     cudaError_t e = cudaSuccess;
 #define ECF(NN)                                                                                               \

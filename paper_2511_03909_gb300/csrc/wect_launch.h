@@ -89,8 +89,9 @@ int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
 cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
 size_t cubical_bwd_rsum_smem(int n, int d, int T, int R);
+// ECF kernels for nf filters: bins [nf][nv], out [nf][T] (blockIdx.y = filter).
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
-                               unsigned long long *out, int64_t nv, cudaStream_t st);
+                               unsigned long long *out, int64_t nv, int nf, cudaStream_t st);
 cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
                                uint16_t *bins, cudaStream_t st);
 cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
@@ -132,7 +133,8 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
                                   uint16_t *bins, unsigned long long *Iacc, float *grad, double scale,
                                   cudaStream_t st);
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
-                               const uint16_t *bins, int T, unsigned long long *out, cudaStream_t st);
+                               const uint16_t *bins, int T, unsigned long long *out, int64_t nv, int nf,
+                               cudaStream_t st);
 
 // common
 cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,

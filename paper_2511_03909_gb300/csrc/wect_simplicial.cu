@@ -620,10 +620,12 @@ __global__ void i128_to_grad_kernel(const unsigned long long *Iacc, int64_t nv, 
 
 template <int M>
 __global__ void simplex_ecf_kernel(const int32_t *simp, const int64_t *sw, int64_t k, int sign, int weighted,
-                                   const uint16_t *bins, int T, unsigned long long *out)
+                                   const uint16_t *bins, int T, unsigned long long *out, int64_t nv)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     long long *h = reinterpret_cast<long long *>(smem);
+    bins += (int64_t)blockIdx.y * nv;       // filter blockIdx.y of [m][nv] bins, row of [m][T] out
+    out += (int64_t)blockIdx.y * T;
     for (int i = threadIdx.x; i < T; i += blockDim.x) h[i] = 0;
     __syncthreads();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
@@ -838,16 +840,17 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
 }
 
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
-                               const uint16_t *bins, int T, unsigned long long *out, cudaStream_t st)
+                               const uint16_t *bins, int T, unsigned long long *out, int64_t nv, int nf,
+                               cudaStream_t st)
 {
     if (k <= 0) return cudaSuccess;
-    const unsigned g = (unsigned)std::min<int64_t>((k + 255) / 256, 1024);
+    const dim3 g((unsigned)std::min<int64_t>((k + 255) / 256, std::max(8, 1024 / std::max(nf, 1))), (unsigned)nf);
     const size_t sm = (size_t)T * 8u;
     cudaError_t e = cudaSuccess;
 #define SE(MM)                                                                                              \
     do {                                                                                                    \
         e = cudaFuncSetAttribute(simplex_ecf_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e == cudaSuccess) simplex_ecf_kernel<MM><<<g, 256, sm, st>>>(simp, sw, k, sign, weighted, bins, T, out); \
+        if (e == cudaSuccess) simplex_ecf_kernel<MM><<<g, 256, sm, st>>>(simp, sw, k, sign, weighted, bins, T, out, nv); \
     } while (0)
     switch (m) {
     case 1: SE(1); break;
