@@ -407,6 +407,23 @@ def extras(P, S, dev):
     cells = len(wv.grids) * cells_of(wv.dims)
     res["volumes3d_256x64^3"] = {"fwd_ms": tf, "fwd_bwd_ms": tfb, "ratio": tfb / tf,
                                  "fwd_evals_per_s": cells * 128 / (tf / 1e3)}
+    del bb, bt, w, flat
+    # intensity-filter ECF of uniform images and volumes (the paper's ECF throughput workloads):
+    # pixels (voxels) per second, T = 1000 and 10000, filter resident on the device
+    g = torch.Generator(device=dev).manual_seed(7)
+    ecf = {}
+    for dims in ([2048] * 2, [4096] * 2, [8192] * 2, [128] * 3, [256] * 3, [512] * 3):
+        nv = 1
+        for L in dims:
+            nv *= L
+        f = torch.rand(nv, generator=g, device=dev, dtype=torch.float64)
+        cx = P.CubicalComplex(None, dims=dims)
+        o = torch.empty(10000, dtype=torch.int64, device=dev)
+        for T in (1000, 10000):
+            ms = timed(lambda: cx.ecf(f, T, 0.0, 1.0, out=o[:T]), reps=5)
+            ecf[f"{'x'.join(map(str, dims))}_T{T}"] = {"ms": ms, "gvertices_per_s": nv / ms / 1e6}
+        del cx, f
+    res["ecf_intensity"] = ecf
     return res
 
 

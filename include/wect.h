@@ -94,6 +94,20 @@ WECT_API wect_status wect_complex_create_cubical(int n, const int64_t *dims, con
                                         wect_complex *out);
 
 /*
+ * The Freudenthal (Kuhn) triangulation of a full grid, built on the device: the paper's
+ * triangulated image (Section 2), an alternative to the cubical complex of the same pixels.
+ * Vertices are the grid points at the grid coordinates above; the k-simplices are the chains
+ * 0 = c_0 < c_1 < ... < c_k of nested axis masks in {0,1}^n anchored at a grid point v, i.e.
+ * {v + c_0, ..., v + c_k}, whenever v + c_k lies in the grid (n! top simplices per unit cube,
+ * closed under faces).  The result is a simplicial complex (every simplicial call applies) whose
+ * simplex weights are the max of their vertex weights.  Arguments as wect_complex_create_cubical.
+ * Errors: as wect_complex_create_simplicial; OUT_OF_MEMORY/CUDA for device failures.
+ */
+WECT_API wect_status wect_complex_create_freudenthal(int n, const int64_t *dims, const void *vertex_weights,
+                                            wect_wtype wtype, int frac_bits, wect_stream stream,
+                                            wect_complex *out);
+
+/*
  * Geometric simplicial complex in R^n (Section 3 "inputs": per dimension a list of vertex
  * index rows and a weight per simplex).
  *   n                ambient dimension, 1..3

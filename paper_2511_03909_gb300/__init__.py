@@ -21,7 +21,7 @@ import torch
 from ._build import LIB as _LIB_PATH
 
 __all__ = [
-    "WectError", "load", "CubicalComplex", "SimplicialComplex", "CubicalBatch", "WECTFunction",
+    "WectError", "load", "CubicalComplex", "FreudenthalComplex", "SimplicialComplex", "CubicalBatch", "WECTFunction",
     "wect", "ecf", "launch_count", "library_path",
 ]
 
@@ -67,6 +67,7 @@ _d = C.c_double
 def _declare(L):
     sig = {
         "wect_complex_create_cubical": (_st, [_i, _p, _p, _i, _i, _p, _p]),
+        "wect_complex_create_freudenthal": (_st, [_i, _p, _p, _i, _i, _p, _p]),
         "wect_complex_create_simplicial": (_st, [_i, _i64, _p, _i, _p, _p, _p, _i, _i, _i, _p, _p, _p]),
         "wect_complex_set_weights": (_st, [_p, _p, _p]),
         "wect_complex_num_vertices": (_i64, [_p]),
@@ -104,7 +105,8 @@ def _declare(L):
 def exported_symbols():
     """Names of the C entry points this binding expects the library to export."""
     return [
-        "wect_complex_create_cubical", "wect_complex_create_simplicial", "wect_complex_set_weights",
+        "wect_complex_create_cubical", "wect_complex_create_freudenthal", "wect_complex_create_simplicial",
+        "wect_complex_set_weights",
         "wect_complex_num_vertices", "wect_complex_cell_counts", "wect_complex_device_status",
         "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
@@ -268,6 +270,28 @@ class CubicalComplex(_Complex):
         h = C.c_void_p()
         _check(L.wect_complex_create_cubical(self.n, dims_a, _ptr(weights), _wtype_of(weights), frac_bits, _stream(),
                                              C.byref(h)))
+        self._h = h
+
+
+class FreudenthalComplex(_Complex):
+    """Freudenthal (Kuhn) triangulation of a full grid, built on the device
+    (wect_complex_create_freudenthal): a simplicial complex.  ``weights`` and ``dims`` as for
+    CubicalComplex."""
+
+    def __init__(self, weights: torch.Tensor | None, frac_bits: int = 0, dims=None):
+        L = load()
+        if weights is not None:
+            _require_cuda(weights, "weights")
+            dims = list(reversed(weights.shape))
+        elif dims is None:
+            raise ValueError("dims is required for an unweighted grid")
+        self.n = len(dims)
+        self.dims = [int(x) for x in dims]
+        self.nv = int(math.prod(self.dims))
+        dims_a = (C.c_int64 * self.n)(*self.dims)
+        h = C.c_void_p()
+        _check(L.wect_complex_create_freudenthal(self.n, dims_a, _ptr(weights), _wtype_of(weights), frac_bits,
+                                                 _stream(), C.byref(h)))
         self._h = h
 
 

@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(256) vertex_bins_kernel(const double *__restri
             const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
             b = exact_bin_from(h, beta, T, b);
         }
-        if (act) bins[v * Dt + col] = (uint16_t)b;
+        // every column gets a valid bin: a column past d (the last tile's padding) carries the
+        // bin of direction d - 1, which the gathers read but never flush
+        bins[v * Dt + col] = (uint16_t)b;
     }
 }
 
@@ -315,7 +317,9 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
                 const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
                 b = exact_bin_from(h, beta, T, b);
             }
-            if (act && v0 + g < nv) bins[v * 32 + lane] = (uint16_t)b;
+            // every column gets a valid bin (a padding column carries direction d - 1's), so the
+            // gathers never read an unwritten entry
+            if (v0 + g < nv) bins[v * 32 + lane] = (uint16_t)b;
             const uint32_t addr = histLane + (uint32_t)b * 128u;
             red_shared_add(addr, w[g].x);
             if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);

@@ -210,6 +210,38 @@ def closure_from_top(coords: np.ndarray, top: np.ndarray) -> Simplicial:
     return Simplicial(coords=np.ascontiguousarray(coords), simplices=lists, weights=np.ones(coords.shape[0], dtype=np.uint8))
 
 
+def freudenthal_lists(dims) -> list:
+    """Index lists of the Freudenthal (Kuhn) triangulation of a full grid (axis 0 fastest): the
+    k-simplices are {v + c_0, ..., v + c_k} for chains 0 = c_0 < ... < c_k of nested axis masks,
+    wherever v + c_k is in the grid.  Lists [edges, triangles, ...] as int32 arrays."""
+    n = len(dims)
+    strides = [1] * n
+    for a in range(1, n):
+        strides[a] = strides[a - 1] * dims[a - 1]
+
+    def chains(last, cur, out):
+        if len(cur) > 1:
+            out.setdefault(len(cur) - 1, []).append(list(cur))
+        for nxt in range(1, 1 << n):
+            if (nxt & last) == last and nxt != last:
+                chains(nxt, cur + [nxt], out)
+
+    by_dim = {}
+    chains(0, [0], by_dim)
+    lists = []
+    for k in range(1, n + 1):
+        rows = []
+        for ch in by_dim.get(k, []):
+            ext = [(ch[-1] >> a) & 1 for a in range(n)]
+            ranges = [range(dims[a] - ext[a]) for a in range(n)]
+            offs = [sum(strides[a] for a in range(n) if (c >> a) & 1) for c in ch]
+            for idx in np.ndindex(*[len(r) for r in reversed(ranges)]):
+                v = sum(i * strides[n - 1 - j] for j, i in enumerate(idx))
+                rows.append([v + o for o in offs])
+        lists.append(np.array(rows, dtype=np.int32).reshape(-1, k + 1))
+    return lists
+
+
 def tetra_grid(side: int, seed: int, jitter: float = 0.2) -> Simplicial:
     """Solid side^3 jittered grid in [-1,1]^3 cut into tetrahedra (six per cube cell, one per
     ordering of the axes: the path lower corner -> +e_a -> +e_a+e_b -> upper corner), with all

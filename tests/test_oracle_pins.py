@@ -341,6 +341,20 @@ def test_brute_force_simplicial_rounding(oracle):
             assert got[p].tolist() == brute_wecf(cx.nv, faces, weights, f, T, beta)
 
 
+def test_freudenthal_triangulation_of_grids(oracle):
+    """The Freudenthal triangulation of a full grid is a triangulated box: Euler characteristic
+    1 at the top threshold in every direction."""
+    for dims in ([6], [5, 4], [3, 4, 3]):
+        n = len(dims)
+        lists = S.freudenthal_lists(dims)
+        X = oracle.grid_coords(dims)
+        nv = X.shape[0]
+        one = oracle.simplicial_weights(lists, np.ones(nv, dtype=np.int64), "one")
+        dirs = S.fibonacci_directions(5) if n == 3 else (S.circle_directions(5) if n == 2 else np.array([[1.0], [-1.0]]))
+        W = oracle.wect_simplicial(X, lists, one, dirs, 9)
+        assert np.all(W[:, -1] == 1)
+
+
 def test_tetrahedral_solid_cube(oracle):
     """Lists with tetrahedra: a triangulated solid cube (six tetrahedra per cell) has Euler
     characteristic 1, and brute-force enumeration of its sublevel subcomplexes (float64
