@@ -407,7 +407,7 @@ def extras(P, S, dev):
     cells = len(wv.grids) * cells_of(wv.dims)
     res["volumes3d_256x64^3"] = {"fwd_ms": tf, "fwd_bwd_ms": tfb, "ratio": tfb / tf,
                                  "fwd_evals_per_s": cells * 128 / (tf / 1e3)}
-    del bb, bt, w, flat
+    del bb, w, flat
     # intensity-filter ECF of uniform images and volumes (the paper's ECF throughput workloads):
     # pixels (voxels) per second, T = 1000 and 10000, filter resident on the device
     g = torch.Generator(device=dev).manual_seed(7)

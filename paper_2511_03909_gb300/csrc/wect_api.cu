@@ -317,7 +317,8 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     int Dmax = 32;
     while (Dmax < d && Dmax < 32 * 4 * warps) Dmax *= 2;
     for (int Dt = (Dt_req > 0 ? Dt_req : Dmax); Dt >= 32; Dt /= 2) {
-        for (int dpl = 4; dpl >= 1; dpl /= 2) {
+        // two directions per lane first (measured fastest on the 128^3 workload), then four, then one
+        for (int dpl : {2, 4, 1}) {
             if (dpl_req > 0 && dpl != dpl_req) continue;
             if (Dt % (32 * dpl)) continue;
             const int WC = Dt / (32 * dpl);

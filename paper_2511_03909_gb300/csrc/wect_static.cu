@@ -138,7 +138,7 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
     int Dmax = 32;
     while (Dmax < d && Dmax < 32 * 4 * warps) Dmax *= 2;
     for (int t = Dmax; t >= 32 && !dpl; t /= 2)
-        for (int p = 4; p >= 1; p /= 2) {
+        for (int p : {2, 4, 1}) {
             if (t % (32 * p) || warps % (t / (32 * p)) || (p > 1 && t / p < 32)) continue;
             const size_t sm = cubical_fwd_smem(n, nsplit, p, T, t, L[0]);
             if (sm > (size_t)optin - 1024) continue;
