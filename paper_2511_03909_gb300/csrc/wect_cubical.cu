@@ -211,7 +211,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
         }
     }
     F2 k02 = f2_pack(k0, k0);
-    const F2 step2 = f2_pack(2.0f * (float)U, 2.0f * (float)U);
+    const F2 two2 = f2_pack(2.0f, 2.0f);
     for (int i0 = 0; i0 < LU; i0 += U) {
         int cv[DPL][U], hv[DPL][U];
 #pragma unroll
@@ -228,15 +228,16 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                 }
             }
         int bad = 0;
+        F2 kk2 = k02;                           // k0 of vertex i0 + u, both halves (exact small integers)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int tlo[DPL], thi[DPL];
             if (DPL % 2 == 0) {
                 // packed pairs of directions: one f32x2 instruction per step for two lanes' slots
-                const F2 kk2 = f2_add_rn(k02, f2_pack(2.0f * (float)u, 2.0f * (float)u));
 #pragma unroll
                 for (int j = 0; j < DPL; j += 2)
                     filter_ceil2(kk2, S0p[j / 2], Glop[j / 2], Ghip[j / 2], M2, tlo[j], thi[j], tlo[j + 1], thi[j + 1]);
+                kk2 = f2_add_rn(kk2, two2);
             } else {
 #pragma unroll
                 for (int j = 0; j < DPL; ++j) filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo[j], thi[j]);
@@ -272,7 +273,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                 }
         }
         k0 += 2.0f * (float)U;
-        k02 = f2_add_rn(k02, step2);
+        k02 = kk2;
     }
     // ragged tail of the row (fewer than U vertices), always clamped
     for (int i0 = LU; i0 < L0; ++i0) {
