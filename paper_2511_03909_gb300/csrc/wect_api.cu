@@ -196,6 +196,7 @@ struct wect_complex_s {
     int frac_bits = 0;
     size_t wbytes = 0;             // bytes per raw vertex weight
     int32_t *d_w32 = nullptr;      // cubical: int32 fixed-point vertex weights read by the kernels
+    double *d_xg = nullptr;        // cubical: grid coordinates [L0 + L1 + L2]
     int nsplit = 1;
     int64_t climit = 0;            // cubical: max |c_o(v)|; simplicial: max |w(s)|
     int kflush = 1 << 16;
@@ -246,6 +247,7 @@ struct wect_batch_s {
     GridDesc *d_grids = nullptr;
     int *d_status = nullptr;
     int32_t *d_w32 = nullptr;      // owned concatenated int32 weights (create_cubical), else nullptr
+    double *d_xg = nullptr;        // owned grid-coordinate tables (create_cubical), else nullptr
     bool owns_w = false;
     Workspace ws;
     std::map<std::pair<int, int>, BatchConfig> tuned;    // (d, T) -> tile shape
@@ -456,6 +458,23 @@ static wect_status upload_items(Workspace &ws, const std::vector<WorkItem> &item
 
 static wect_status pack_simplicial_weights(wect_complex c, cudaStream_t st);
 
+// Grid coordinates x_a(i) = (2i - (L_a-1)) / (L_a-1) (0 when L_a = 1) of every axis of a grid,
+// axis 0 first: one correctly rounded float64 division each, as grid_coord on the device.
+static void append_grid_coords(const int *L, std::vector<double> &out)
+{
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < L[a]; ++i)
+            out.push_back(L[a] <= 1 ? 0.0 : (double)(2 * i - (L[a] - 1)) / (double)(L[a] - 1));
+}
+
+static cudaError_t upload_doubles(const std::vector<double> &h, double **d, cudaStream_t st)
+{
+    cudaError_t e = cudaMalloc((void **)d, std::max<size_t>(h.size(), 1) * sizeof(double));
+    if (e == cudaSuccess && !h.empty()) e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
 static wect_status new_status_word(int **p)
 {
     CK(cudaMalloc((void **)p, sizeof(int)), "alloc");
@@ -520,6 +539,11 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     if ((e = launch_weights_to_w32(wtype, vertex_weights, nv, c->frac_bits, c->climit >> n, c->d_w32, c->d_status, st)))
         return cleanup(cuda_fail(e, "weights_to_w32"));
     g_launches++;
+    {
+        std::vector<double> xg;
+        append_grid_coords(c->L, xg);
+        if ((e = upload_doubles(xg, &c->d_xg, st))) return cleanup(cuda_fail(e, "grid coordinates"));
+    }
     GridDesc g{};
     g.w = c->d_w32;
     for (int a = 0; a < 3; ++a) g.L[a] = c->L[a];
@@ -527,6 +551,7 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     g.nv = nv;
     g.v_off = 0;
     g.status = c->d_status;
+    g.xg = c->d_xg;
     e = cudaMalloc((void **)&c->d_grid, sizeof(GridDesc));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -697,6 +722,7 @@ extern "C" void wect_complex_destroy(wect_complex c)
     if (!c) return;
     cudaDeviceSynchronize();
     if (c->d_w32) cudaFree(c->d_w32);
+    if (c->d_xg) cudaFree(c->d_xg);
     if (c->d_coords) cudaFree(c->d_coords);
     if (c->d_xf) cudaFree(c->d_xf);
     for (int i = 0; i < 4; ++i) {
@@ -1114,6 +1140,7 @@ extern "C" wect_status wect_batch_create(int count, const wect_complex *cxs, wec
         g.rows = g.L[1] * g.L[2];
         g.nv = cxs[i]->nv;
         g.status = cxs[i]->d_status;
+        g.xg = cxs[i]->d_xg;
         b->h_grids[i] = g;
     }
     cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
@@ -1164,6 +1191,16 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_w32, (size_t)total * sizeof(int32_t));
     if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc batch"); }
     b->owns_w = true;
+    {
+        std::vector<double> xg;
+        std::vector<size_t> xoff(count);
+        for (int i = 0; i < count; ++i) {
+            xoff[i] = xg.size();
+            append_grid_coords(b->h_grids[i].L, xg);
+        }
+        if ((e = upload_doubles(xg, &b->d_xg, st))) { wect_batch_destroy(b); return cuda_fail(e, "grid coordinates"); }
+        for (int i = 0; i < count; ++i) b->h_grids[i].xg = b->d_xg + xoff[i];
+    }
     int64_t off = 0;
     for (int i = 0; i < count; ++i) {
         b->h_grids[i].w = b->d_w32 + off;
@@ -1464,6 +1501,7 @@ extern "C" void wect_batch_destroy(wect_batch b)
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_status) cudaFree(b->d_status);
     if (b->owns_w && b->d_w32) cudaFree(b->d_w32);
+    if (b->d_xg) cudaFree(b->d_xg);
     b->ws.release();
     delete b;
 }

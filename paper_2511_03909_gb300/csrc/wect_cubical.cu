@@ -159,7 +159,7 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
 {
     const int T = P.T;
     const int bt = clamp_bin(thi, nr, T);
-    const double h = height3<N>(grid_coord(i0, g.L[0]), grid_coord(i1, g.L[1]), grid_coord(i2, g.L[2]),
+    const double h = height3<N>(gcoord(g, 0, i0), gcoord(g, 1, i1), gcoord(g, 2, i2),
                                 P.dirs + (int64_t)p * N);
     const int be = exact_bin_from(h, P.beta, T, bt);
     if (be == bt) return;

@@ -266,14 +266,12 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
                             const double *sp = P.dirs + (int64_t)P.perm[k] * N;
                             if (tA[u] != hA[u]) {
                                 const int cand = (int)((adA[u] - ssAddr) >> 3) - k * T;
-                                const double h = height3<N>(grid_coord(ia, L0), grid_coord(i1, g.L[1]),
-                                                            grid_coord(i2, g.L[2]), sp);
+                                const double h = height3<N>(gcoord(g, 0, ia), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
                                 accA += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adA[u]);
                             }
                             if (tB[u] != hB[u]) {
                                 const int cand = (int)((adB[u] - ssAddr) >> 3) - k * T;
-                                const double h = height3<N>(grid_coord(ib, L0), grid_coord(i1, g.L[1]),
-                                                            grid_coord(i2, g.L[2]), sp);
+                                const double h = height3<N>(gcoord(g, 0, ib), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
                                 accB += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adB[u]);
                             }
                         }

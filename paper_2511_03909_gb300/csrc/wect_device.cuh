@@ -39,6 +39,7 @@ struct GridDesc {
     int64_t nv;          // vertex count
     int64_t v_off;       // vertex offset of this complex in concatenated per-vertex arrays
     int *status;         // device status word of the complex
+    const double *xg;    // grid coordinates [L0 + L1 + L2] (axis 0, then 1, then 2), or null
 };
 
 // A unit of work of the cubical kernels: one complex, one direction tile, a row range.
@@ -54,6 +55,14 @@ __device__ __forceinline__ double grid_coord(int i, int L)
 {
     if (L <= 1) return 0.0;
     return __ddiv_rn((double)(2 * i - (L - 1)), (double)(L - 1));
+}
+
+// Grid coordinate of index i on axis a, from the complex's table when it has one (the same
+// correctly rounded quotient as grid_coord, computed once when the complex is created).
+__device__ __forceinline__ double gcoord(const GridDesc &g, int a, int i)
+{
+    if (g.xg) return __ldg(g.xg + (a >= 1 ? g.L[0] : 0) + (a >= 2 ? g.L[1] : 0) + i);
+    return grid_coord(i, g.L[a]);
 }
 
 // h = x[n-1]*s[n-1], then fma from n-2 down to 0 (every op rounded on its own).
