@@ -176,6 +176,52 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
     }
 }
 
+// The undecided (vertex, direction) pairs of one block of U vertices, spread over the warp: every
+// lane lists its pairs (bit u * DPL + j of pend) in a per-warp queue of 32 entries, and each lane
+// then fixes one queued pair, whoever found it.  Lanes whose direction meets many exact ties
+// (regular grids seen along axis or diagonal directions) no longer serialise the warp.
+template <int N, int NSPLIT, int DPL>
+__device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow,
+                                                 int CP, int i0, int i1, int i2, uint32_t pend, float k0,
+                                                 const DirFilter *dirf, int colbase, int pbase, uint32_t histAddr,
+                                                 int Dt, uint32_t HOFF, uint32_t *wq)
+{
+    constexpr int NOCT = 1 << N;
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(pend);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int first = incl - cnt;
+    for (int base = 0; base < total; base += 32) {
+        uint32_t rest = pend;
+        for (int q = first; rest; ++q) {
+            const int bit = __ffs(rest) - 1;
+            rest &= rest - 1;
+            if (q >= base && q < base + 32) wq[q - base] = ((uint32_t)lane << 8) | (uint32_t)bit;
+        }
+        __syncwarp();
+        if (base + lane < total) {
+            const uint32_t e = wq[lane];
+            const int src = (int)(e >> 8), bit = (int)(e & 255u), u = bit / DPL, j = bit % DPL;
+            const int col = colbase + j * 32 + src;
+            const DirFilter f = dirf[col];
+            const RowFilter rf = make_row_filter<N>(f, i1, i2, g.L);
+            int tlo, thi;
+            filter_ceil(k0 + 2.0f * (float)u, f.S0, rf.Glo, rf.Ghi, tlo, thi);
+            const int cv = crow[f.oct * CP + i0 + u];
+            const int hv = (NSPLIT == 2) ? crow[NOCT * CP + f.oct * CP + i0 + u] : 0;
+            cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col], i0 + u, i1, i2, thi, rf.nr, col, histAddr, Dt, HOFF, cv,
+                                     hv);
+        }
+        __syncwarp();
+    }
+}
+
 // One grid row for the DPL directions of each lane.  CLAMP selects the variant whose bins may
 // leave [0, T-1] (heights outside the threshold range); the other variant has been proven
 // in range for the whole row and skips the clamp.
@@ -183,7 +229,7 @@ template <int N, int NSPLIT, int DPL, bool CLAMP>
 __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow, int CP, int L0,
                                         int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
                                         const int (&oct)[DPL], const int (&col)[DPL], int pbase, uint32_t histAddr,
-                                        int Dt, uint32_t HOFF)
+                                        int Dt, uint32_t HOFF, const DirFilter *dirf, int colbase, uint32_t *wq)
 {
     constexpr int NOCT = 1 << N;
     constexpr int U = (NSPLIT == 1 && DPL <= 2) ? 8 : 4;
@@ -261,16 +307,17 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             }
         }
         if (__any_sync(0xffffffffu, bad != 0)) {
+            uint32_t pend = 0;
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int j = 0; j < DPL; ++j) {
                     int tlo, thi;
                     filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
-                    if (tlo != thi)
-                        cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col[j]], i0 + u, i1, i2, thi, rf[j].nr, col[j],
-                                                 histAddr, Dt, HOFF, cv[j][u], hv[j][u]);
+                    if (tlo != thi) pend |= 1u << (u * DPL + j);
                 }
+            cubical_fixup_block<N, NSPLIT, DPL>(P, g, crow, CP, i0, i1, i2, pend, k0, dirf, colbase, pbase, histAddr, Dt,
+                                                HOFF, wq);
         }
         k0 += 2.0f * (float)U;
         k02 = kk2;
@@ -330,6 +377,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     const int rowbuf = NSPLIT * NOCT * CP;                                       // words of one row buffer
     const int nbuf = (WC == 1) ? 1 : 2;     // a one-warp group needs no second buffer (warp-synchronous)
     int32_t *cgrp = reinterpret_cast<int32_t *>(dirf + Dt) + rgroup * nbuf * rowbuf;
+    uint32_t *wq = reinterpret_cast<uint32_t *>(reinterpret_cast<int32_t *>(dirf + Dt) + RG * nbuf * rowbuf) + wid * 32;
     const uint32_t histAddr = smem_addr(hist);
     const uint32_t HOFF = (uint32_t)histWords * 4u;
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
@@ -411,9 +459,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
                 clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
             }
             if (__any_sync(0xffffffffu, clampRow))
-                fwd_row<N, NSPLIT, DPL, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF);
+                fwd_row<N, NSPLIT, DPL, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF,
+                                              dirf, wcol * 32 * DPL, wq);
             else
-                fwd_row<N, NSPLIT, DPL, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF);
+                fwd_row<N, NSPLIT, DPL, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF,
+                                               dirf, wcol * 32 * DPL, wq);
         }
         __syncthreads();
         if (P.direct)
@@ -556,7 +606,9 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0)
     const int RG = (kFwdThreads / 32) / WC;
     const size_t rowbuf = (size_t)nsplit * noct * cubical_fwd_pitch(maxL0);
     const int nbuf = (WC == 1) ? 1 : 2;
-    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u;
+    // + one 32-entry fix-up queue per warp
+    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u +
+           (size_t)(kFwdThreads / 32) * 32u * 4u;
 }
 
 int cubical_fwd_threads() { return kFwdThreads; }
