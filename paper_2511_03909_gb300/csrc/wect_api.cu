@@ -1040,6 +1040,9 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     a.scale_dev = scale_dev;
     a.frac_bits = frac_bits;
     a.total_nv = total_nv;
+    a.uniform_nv = h_grids.empty() ? 0 : h_grids[0].nv;
+    for (const auto &hg : h_grids)
+        if (hg.nv != a.uniform_nv) a.uniform_nv = 0;
     {
         ProfScope prof(st);
         KL(launch_cubical_bwd(n, a, ws.n_items_bwd, sm, st), "cubical_bwd");

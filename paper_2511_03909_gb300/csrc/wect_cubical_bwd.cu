@@ -363,7 +363,9 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
     const int64_t gid = P.v_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= P.v_end) return;
     int cx = 0;
-    if (P.n_grids > 1) {
+    if (P.uniform_nv > 0) {
+        cx = (int)(gid / P.uniform_nv);         // every grid of the batch has the same vertex count
+    } else if (P.n_grids > 1) {
         int hi_c = P.n_grids - 1;
         while (cx < hi_c) {
             const int mid = (cx + hi_c + 1) >> 1;

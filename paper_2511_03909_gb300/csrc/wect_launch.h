@@ -45,6 +45,7 @@ struct CubicalBwdArgs {
     const double *scale_dev;      // when set, the scale is read from the device (quantised upstream)
     int frac_bits;
     int64_t total_nv;
+    int64_t uniform_nv;           // vertex count shared by every grid (0 when they differ)
 };
 
 struct SimplexFwdArgs {
