@@ -320,6 +320,16 @@ WECT_API int64_t wect_kernel_launch_count(void);
 WECT_API wect_status wect_profile_enable(int on);
 WECT_API wect_status wect_profile_read(double *kernel_ms, int64_t *launches);
 
+/*
+ * Allocation-failure injection, a test hook for the error paths.  With k >= 0 the next k
+ * device allocations the library makes (in any call, on any thread) succeed and the one after
+ * fails as if the device were out of memory: the call that made it returns
+ * WECT_ERR_OUT_OF_MEMORY, frees what it had allocated, and leaves its handles and outputs as
+ * they were.  The failing allocation disarms the hook; k < 0 disarms it at once.  No CUDA
+ * call fails for real, so the context stays usable.  Always returns WECT_OK.
+ */
+WECT_API wect_status wect_debug_fail_alloc(int64_t k);
+
 #ifdef __cplusplus
 }
 #endif

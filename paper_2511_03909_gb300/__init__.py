@@ -95,6 +95,7 @@ def _declare(L):
         "wect_profile_enable": (_st, [_i]),
         "wect_profile_read": (_st, [_p, _p]),
         "wect_cubical_compute_static": (_st, [_i, _p, _p, _i, _p, _i, _i, _d, _d, _p, _p]),
+        "wect_debug_fail_alloc": (_st, [_i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -113,7 +114,7 @@ def exported_symbols():
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
         "wect_batch_autotune",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
-        "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static",
+        "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_debug_fail_alloc",
     ]
 
 
@@ -161,6 +162,12 @@ def profile_read():
     n = C.c_int64()
     _check(load().wect_profile_read(C.byref(ms), C.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def debug_fail_alloc(k: int):
+    """Test hook: the next k device allocations of the library succeed and the one after fails
+    as out of memory (k < 0 disarms)."""
+    _check(load().wect_debug_fail_alloc(int(k)))
 
 
 def version() -> str:

@@ -34,9 +34,25 @@ static wect_status fail(wect_status st, const char *fmt, ...)
     return st;
 }
 
+// Allocation-failure injection for tests: the number of device allocations that still succeed
+// before one fails (-1: disarmed).  The failing allocation disarms the hook.
+static std::atomic<int64_t> g_alloc_fail_in{-1};
+
 namespace wect {
 void note_error(const char *msg) { g_last_error = msg; }
 void note_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    int64_t k = g_alloc_fail_in.load();
+    while (k >= 0 && !g_alloc_fail_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 }  // namespace wect
 
 static wect_status cuda_fail(cudaError_t e, const char *where)
@@ -145,7 +161,7 @@ struct DBuf {
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
-        cudaError_t e = cudaMalloc((void **)&p, std::max<size_t>(n, 1) * sizeof(T));
+        cudaError_t e = dev_malloc((void **)&p, std::max<size_t>(n, 1) * sizeof(T));
         if (e == cudaSuccess) cap = std::max<size_t>(n, 1);
         return e;
     }
@@ -222,10 +238,23 @@ struct wect_complex_s {
     std::mutex mu;
 };
 
+// What a captured forward graph reads from the batch's workspace besides the arguments in its
+// key: the buffers' addresses and the uploaded item list (named by its key).  A later call with
+// other sizes may grow a buffer (new address) or upload other items; the graph is then stale.
+using GraphDeps = std::tuple<const void *, const void *, const void *, const void *, const void *, const void *,
+                             const void *, std::tuple<int, int, int, int, int>, int>;
+
+static GraphDeps graph_deps(const Workspace &ws)
+{
+    return GraphDeps(ws.M.p, ws.range.p, ws.beta.p, ws.perm.p, ws.octb.p, ws.counter.p, ws.items.p, ws.items_key,
+                     ws.n_items);
+}
+
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int nodes = 0;
+    GraphDeps deps{};
 };
 
 struct BatchConfig {
@@ -446,6 +475,8 @@ static wect_status ensure_common_ws(Workspace &ws, int T, int d = 1)
 
 static wect_status upload_items(Workspace &ws, const std::vector<WorkItem> &items, cudaStream_t st)
 {
+    ws.items_key = std::make_tuple(-1, -1, -1, -1, -1);     // the callers set it once the upload is done
+    ws.n_items = 0;
     CK(ws.items.ensure(items.size()), "alloc");
     CK(cudaMemcpyAsync(ws.items.p, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st),
        "upload items");
@@ -469,7 +500,7 @@ static void append_grid_coords(const int *L, std::vector<double> &out)
 
 static cudaError_t upload_doubles(const std::vector<double> &h, double **d, cudaStream_t st)
 {
-    cudaError_t e = cudaMalloc((void **)d, std::max<size_t>(h.size(), 1) * sizeof(double));
+    cudaError_t e = dev_malloc((void **)d, std::max<size_t>(h.size(), 1) * sizeof(double));
     if (e == cudaSuccess && !h.empty()) e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
@@ -477,7 +508,7 @@ static cudaError_t upload_doubles(const std::vector<double> &h, double **d, cuda
 
 static wect_status new_status_word(int **p)
 {
-    CK(cudaMalloc((void **)p, sizeof(int)), "alloc");
+    CK(dev_malloc((void **)p, sizeof(int)), "alloc");
     CK(cudaMemset(*p, 0, sizeof(int)), "memset");
     return WECT_OK;
 }
@@ -535,7 +566,7 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     }
     if ((s = choose_cubical_mode(n, wtype, wmax, c->nsplit, c->climit, c->kflush))) return cleanup(s);
     if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st))) return cleanup(cuda_fail(e, "memset"));
-    if ((e = cudaMalloc((void **)&c->d_w32, (size_t)nv * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc weights"));
+    if ((e = dev_malloc((void **)&c->d_w32, (size_t)nv * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc weights"));
     if ((e = launch_weights_to_w32(wtype, vertex_weights, nv, c->frac_bits, c->climit >> n, c->d_w32, c->d_status, st)))
         return cleanup(cuda_fail(e, "weights_to_w32"));
     g_launches++;
@@ -552,7 +583,7 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     g.v_off = 0;
     g.status = c->d_status;
     g.xg = c->d_xg;
-    e = cudaMalloc((void **)&c->d_grid, sizeof(GridDesc));
+    e = dev_malloc((void **)&c->d_grid, sizeof(GridDesc));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "upload grid"));
@@ -603,17 +634,17 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
     if ((s = new_status_word(&c->d_status))) return cleanup(s);
     if ((s = ensure_common_ws(c->ws, 2))) return cleanup(s);
     int *d_bad = nullptr;
-    if ((e = cudaMalloc((void **)&d_bad, 4 * sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "alloc"));
+    if ((e = dev_malloc((void **)&d_bad, 4 * sizeof(int))) != cudaSuccess) return cleanup(cuda_fail(e, "alloc"));
     struct FreeBad { int *p; ~FreeBad() { if (p) cudaFree(p); } } fb{d_bad};
     if ((e = cudaMemsetAsync(d_bad, 0, 4 * sizeof(int), st)) != cudaSuccess) return cleanup(cuda_fail(e, "memset"));
     // coordinates
-    if ((e = cudaMalloc((void **)&c->d_coords, (size_t)n_vertices * n * sizeof(double))) != cudaSuccess)
+    if ((e = dev_malloc((void **)&c->d_coords, (size_t)n_vertices * n * sizeof(double))) != cudaSuccess)
         return cleanup(cuda_fail(e, "alloc coords"));
     if ((e = cudaMemcpyAsync(c->d_coords, coords, (size_t)n_vertices * n * sizeof(double), cudaMemcpyDeviceToDevice, st)))
         return cleanup(cuda_fail(e, "copy coords"));
     if ((e = launch_finite_check(c->d_coords, n_vertices * n, d_bad + 0, 1, st))) return cleanup(cuda_fail(e, "finite_check"));
     g_launches++;
-    if ((e = cudaMalloc((void **)&c->d_xf, (size_t)n_vertices * n * sizeof(float))) != cudaSuccess)
+    if ((e = dev_malloc((void **)&c->d_xf, (size_t)n_vertices * n * sizeof(float))) != cudaSuccess)
         return cleanup(cuda_fail(e, "alloc coords"));
     if ((e = launch_coords_to_f32(c->d_coords, n_vertices * n, c->d_xf, st))) return cleanup(cuda_fail(e, "coords_to_f32"));
     g_launches++;
@@ -628,7 +659,7 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
     // simplex lists
     for (int i = 1; i <= max_dim; ++i) {
         const size_t cnt = (size_t)counts[i] * (i + 1);
-        if ((e = cudaMalloc((void **)&c->d_simp[i], std::max<size_t>(cnt, 1) * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc"));
+        if ((e = dev_malloc((void **)&c->d_simp[i], std::max<size_t>(cnt, 1) * sizeof(int32_t)))) return cleanup(cuda_fail(e, "alloc"));
         if (cnt) {
             if ((e = cudaMemcpyAsync(c->d_simp[i], simplices[i], cnt * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)))
                 return cleanup(cuda_fail(e, "copy simplices"));
@@ -638,7 +669,7 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
     }
     // weights
     for (int i = 0; i <= max_dim; ++i)
-        if ((e = cudaMalloc((void **)&c->d_sw[i], std::max<int64_t>(counts[i], 1) * sizeof(int64_t))))
+        if ((e = dev_malloc((void **)&c->d_sw[i], std::max<int64_t>(counts[i], 1) * sizeof(int64_t))))
             return cleanup(cuda_fail(e, "alloc weights"));
     if ((e = cudaMemsetAsync(c->ws.M.p, 0, 2 * sizeof(unsigned long long), st))) return cleanup(cuda_fail(e, "memset"));
     if (vw_explicit) {
@@ -696,7 +727,7 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
         if (counts[i] > 1 && (e = sort_simplices_by_min_vertex(c->d_simp[i], counts[i], i + 1, c->d_sw[i], n_vertices, st)))
             return cleanup(cuda_fail(e, "sort lists"));
     for (int i = 0; i <= max_dim; ++i)
-        if ((e = cudaMalloc((void **)&c->d_swp[i], std::max<int64_t>(counts[i], 1) * sizeof(int2))))
+        if ((e = dev_malloc((void **)&c->d_swp[i], std::max<int64_t>(counts[i], 1) * sizeof(int2))))
             return cleanup(cuda_fail(e, "alloc packed weights"));
     if ((s = pack_simplicial_weights(c, st))) return cleanup(s);
     // chunk-local ids of the lists of dim >= 1, for the staged gather (indices are valid here)
@@ -704,9 +735,9 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
         if (counts[i] == 0) continue;
         const int m = i + 1;
         const int64_t nch = (counts[i] + chunk_simplices(m) - 1) / chunk_simplices(m);
-        if ((e = cudaMalloc((void **)&c->d_local[i], (size_t)counts[i] * m * sizeof(uint16_t))) ||
-            (e = cudaMalloc((void **)&c->d_cverts[i], (size_t)nch * kWinRows * sizeof(int32_t))) ||
-            (e = cudaMalloc((void **)&c->d_cnu[i], (size_t)nch * sizeof(int32_t))))
+        if ((e = dev_malloc((void **)&c->d_local[i], (size_t)counts[i] * m * sizeof(uint16_t))) ||
+            (e = dev_malloc((void **)&c->d_cverts[i], (size_t)nch * kWinRows * sizeof(int32_t))) ||
+            (e = dev_malloc((void **)&c->d_cnu[i], (size_t)nch * sizeof(int32_t))))
             return cleanup(cuda_fail(e, "alloc chunks"));
         if ((e = launch_chunk_local(c->d_simp[i], counts[i], m, c->d_local[i], c->d_cverts[i], c->d_cnu[i], st)))
             return cleanup(cuda_fail(e, "chunk_local"));
@@ -1003,6 +1034,8 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
             const int per = std::max(R, ((std::max(1, 65536 / std::max(1, h_grids[c].L[0])) + R - 1) / R) * R);
             for (int r0 = 0; r0 < rows; r0 += per) items.push_back(WorkItem{c, 0, r0, std::min(rows, r0 + per)});
         }
+        ws.items_bwd_key = std::make_tuple(-1, -1);         // set again once the upload is done
+        ws.n_items_bwd = 0;
         CK(ws.items_bwd.ensure(items.size()), "alloc");
         CK(cudaMemcpyAsync(ws.items_bwd.p, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st), "upload");
         CK(cudaStreamSynchronize(st), "sync");
@@ -1101,7 +1134,7 @@ static wect_status batch_finish(wect_batch b, cudaStream_t st)
         b->maxL0 = std::max(b->maxL0, b->h_grids[i].L[0]);
     }
     b->total_nv = off;
-    CK(cudaMalloc((void **)&b->d_grids, b->h_grids.size() * sizeof(GridDesc)), "alloc grids");
+    CK(dev_malloc((void **)&b->d_grids, b->h_grids.size() * sizeof(GridDesc)), "alloc grids");
     CK(cudaMemcpy(b->d_grids, b->h_grids.data(), b->h_grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice), "upload grids");
     CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
     (void)st;
@@ -1146,7 +1179,7 @@ extern "C" wect_status wect_batch_create(int count, const wect_complex *cxs, wec
         g.xg = cxs[i]->d_xg;
         b->h_grids[i] = g;
     }
-    cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
+    cudaError_t e = dev_malloc((void **)&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
     if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc"); }
     wect_status s = batch_finish(b, nullptr);
@@ -1189,9 +1222,9 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
         b->h_grids[i] = g;
         total += nv;
     }
-    cudaError_t e = cudaMalloc((void **)&b->d_status, sizeof(int));
+    cudaError_t e = dev_malloc((void **)&b->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_w32, (size_t)total * sizeof(int32_t));
+    if (e == cudaSuccess) e = dev_malloc((void **)&b->d_w32, (size_t)total * sizeof(int32_t));
     if (e != cudaSuccess) { wect_batch_destroy(b); return cuda_fail(e, "alloc batch"); }
     b->owns_w = true;
     {
@@ -1214,7 +1247,7 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
     uint64_t wmax = 255;
     if (wtype == WECT_W_F32 || wtype == WECT_W_I64_FIXED) {
         int *d_bad = nullptr;
-        e = cudaMalloc((void **)&d_bad, sizeof(int));
+        e = dev_malloc((void **)&d_bad, sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.M.p, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = launch_weights_to_fixed(wtype, vertex_weights, total, b->frac_bits, nullptr, b->ws.M.p, d_bad, st);
@@ -1303,6 +1336,13 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     if ((s = batch_items(b, d, T, sh, direct, st))) return s;
     auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.dpl);
     auto it = b->graphs.find(key);
+    if (it != b->graphs.end() && it->second.deps != graph_deps(b->ws)) {
+        CK(cudaStreamSynchronize(st), "sync");          // a replay of it may still be running
+        cudaGraphExecDestroy(it->second.exec);
+        cudaGraphDestroy(it->second.graph);
+        b->graphs.erase(it);
+        it = b->graphs.end();
+    }
     if (it == b->graphs.end()) {
         // capture the launch sequence once on a private stream, replay it on the caller's stream
         CK(prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.smem), "prepare");
@@ -1315,6 +1355,7 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
         if (s2) return s2;
         if (e != cudaSuccess) return cuda_fail(e, "end capture");
         ge.nodes = (int)(g_launches.load() - before);
+        ge.deps = graph_deps(b->ws);
         g_launches -= ge.nodes;          // counted at each replay instead
         if ((e = cudaGraphInstantiate(&ge.exec, ge.graph, 0)) != cudaSuccess) {
             cudaGraphDestroy(ge.graph);
@@ -1514,6 +1555,12 @@ extern "C" void wect_batch_destroy(wect_batch b)
 extern "C" const char *wect_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *wect_version(void) { return "wect-gb300 0.1 (sm_103a)"; }
 extern "C" int64_t wect_kernel_launch_count(void) { return g_launches.load(); }
+
+extern "C" wect_status wect_debug_fail_alloc(int64_t k)
+{
+    g_alloc_fail_in.store(k < 0 ? -1 : k);
+    return WECT_OK;
+}
 
 extern "C" wect_status wect_profile_enable(int on)
 {

@@ -92,7 +92,7 @@ extern "C" wect_status wect_complex_create_freudenthal(int n, const int64_t *dim
     int32_t *lists[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t counts[4] = {nv, 0, 0, 0};
     wect_status status = WECT_OK;
-    cudaError_t e = cudaMalloc((void **)&coords, (size_t)nv * n * sizeof(double));
+    cudaError_t e = dev_malloc((void **)&coords, (size_t)nv * n * sizeof(double));
     if (e == cudaSuccess) {
         grid_coords_kernel<<<(unsigned)std::min<int64_t>((nv + 255) / 256, 152 * 16), 256, 0, st>>>(n, L[0], L[1], L[2],
                                                                                                     nv, coords);
@@ -121,7 +121,7 @@ extern "C" wect_status wect_complex_create_freudenthal(int n, const int64_t *dim
             counts[k] += cnt;
         }
         if (counts[k] == 0) continue;
-        if ((e = cudaMalloc((void **)&lists[k], (size_t)counts[k] * (k + 1) * sizeof(int32_t)))) break;
+        if ((e = dev_malloc((void **)&lists[k], (size_t)counts[k] * (k + 1) * sizeof(int32_t)))) break;
         int64_t base = 0;
         for (size_t t = 0; t < types.size(); ++t) {
             if (tcount[t] > 0) {
@@ -135,7 +135,7 @@ extern "C" wect_status wect_complex_create_freudenthal(int n, const int64_t *dim
     }
     if (e != cudaSuccess) {
         note_error(cudaGetErrorString(e));
-        status = WECT_ERR_CUDA;
+        status = e == cudaErrorMemoryAllocation ? WECT_ERR_OUT_OF_MEMORY : WECT_ERR_CUDA;
     } else {
         int max_dim = 0;
         for (int k = 1; k <= n; ++k)

@@ -165,5 +165,7 @@ cudaError_t launch_index_check(const int32_t *idx, int64_t n, int64_t nv, int *b
 // host-side bookkeeping shared with the C entry points (last error message, launch counter)
 void note_error(const char *msg);
 void note_launches(int64_t n);
+// cudaMalloc behind the library's allocation-failure test hook (wect_debug_fail_alloc).
+cudaError_t dev_malloc(void **p, size_t bytes);
 
 }  // namespace wect

@@ -47,15 +47,15 @@ cudaError_t sort_simplices_by_min_vertex(int32_t *simp, int64_t k, int m, int64_
     cudaError_t e = cudaSuccess;
     const unsigned g = (unsigned)std::min<int64_t>((k + 255) / 256, 152 * 16);
     do {
-        if ((e = cudaMalloc((void **)&key, k * sizeof(int32_t))) || (e = cudaMalloc((void **)&key2, k * sizeof(int32_t))) ||
-            (e = cudaMalloc((void **)&idx, k * sizeof(int32_t))) || (e = cudaMalloc((void **)&idx2, k * sizeof(int32_t))) ||
-            (e = cudaMalloc((void **)&simp2, (size_t)k * m * sizeof(int32_t))))
+        if ((e = dev_malloc((void **)&key, k * sizeof(int32_t))) || (e = dev_malloc((void **)&key2, k * sizeof(int32_t))) ||
+            (e = dev_malloc((void **)&idx, k * sizeof(int32_t))) || (e = dev_malloc((void **)&idx2, k * sizeof(int32_t))) ||
+            (e = dev_malloc((void **)&simp2, (size_t)k * m * sizeof(int32_t))))
             break;
-        if (sw && (e = cudaMalloc((void **)&sw2, k * sizeof(int64_t)))) break;
+        if (sw && (e = dev_malloc((void **)&sw2, k * sizeof(int64_t)))) break;
         min_vertex_kernel<<<g, 256, 0, st>>>(simp, k, m, key, idx);
         if ((e = cudaGetLastError())) break;
         if ((e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, key2, idx, idx2, (int)k, 0, bits, st))) break;
-        if ((e = cudaMalloc(&tmp, tmp_bytes))) break;
+        if ((e = dev_malloc(&tmp, tmp_bytes))) break;
         if ((e = cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, key, key2, idx, idx2, (int)k, 0, bits, st))) break;
         gather_simplices_kernel<<<g, 256, 0, st>>>(simp, sw, k, m, idx2, simp2, sw2);
         if ((e = cudaGetLastError())) break;
@@ -63,6 +63,7 @@ cudaError_t sort_simplices_by_min_vertex(int32_t *simp, int64_t k, int m, int64_
         if (sw && (e = cudaMemcpyAsync(sw, sw2, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, st))) break;
         e = cudaStreamSynchronize(st);          // before the temporaries are freed
     } while (0);
+    if (e != cudaSuccess) cudaStreamSynchronize(st);    // work queued before the failure uses them too
     cudaFree(key);
     cudaFree(key2);
     cudaFree(idx);
