@@ -501,7 +501,7 @@ def extras(P, S, dev):
 
 def run_case(name):
     """Run one small workload a few times, untimed, for ncu captures of kernels the headline
-    step does not launch (the adjoint and the simplicial gather)."""
+    step does not launch (the adjoint, the simplicial gather, the batch, the ECF)."""
     import torch
 
     sys.path.insert(0, ROOT)
@@ -531,6 +531,38 @@ def run_case(name):
             W = h.wect(dirs, wl.T, -1.5, 1.5)
         torch.cuda.synchronize()
         print("mesh64 ok", int(W[:, -1].abs().sum()))
+    elif name == "batch4096":
+        # the 4096-image batch (d = 64, T = 64, [-sqrt2, sqrt2]): two graph replays, then one
+        # per-image launch loop
+        wl = S.image_batch()
+        dirs = torch.from_numpy(wl.dirs).to(dev)
+        b = P.CubicalBatch([torch.from_numpy(x).to(dev) for x in wl.grids])
+        out = torch.empty((len(wl.grids), 64, 64), dtype=torch.int64, device=dev)
+        for _ in range(2):
+            b.wect(dirs, wl.T, wl.lo, wl.hi, out=out)
+        b.wect(dirs, wl.T, wl.lo, wl.hi, out=out, loop=True)
+        torch.cuda.synchronize()
+        print("batch4096 ok", int(out[:, :, -1].sum()))
+    elif name == "ecf4096":
+        # intensity-filter ECF of a uniform 4096^2 image, T = 1000, [0, 1]: three calls
+        g = torch.Generator(device=dev).manual_seed(7)
+        f = torch.rand(4096 * 4096, generator=g, device=dev, dtype=torch.float64)
+        cx = P.CubicalComplex(None, dims=[4096, 4096])
+        for _ in range(3):
+            o = cx.ecf(f, 1000, 0.0, 1.0)
+        torch.cuda.synchronize()
+        print("ecf4096 ok", int(o[-1]))
+    elif name == "wecf64":
+        # 64 uniform vertex filters on the 128^3 cubical complex of the voxel workload, T = 128,
+        # [-1, 1], weighted: three calls
+        wl = S.voxel3d_128()
+        cx = P.CubicalComplex(torch.from_numpy(wl.grid).to(dev))
+        g = torch.Generator(device=dev).manual_seed(3)
+        F = torch.rand((64, cx.nv), generator=g, device=dev, dtype=torch.float64) * 2 - 1
+        for _ in range(3):
+            o = cx.wecf(F, 128, -1.0, 1.0)
+        torch.cuda.synchronize()
+        print("wecf64 ok", int(o[:, -1].sum()))
     else:
         raise SystemExit(f"unknown case {name}")
     return 0
@@ -544,7 +576,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", action="store_true", help="also time the batched and differentiation workloads")
-    ap.add_argument("--case", choices=["adjoint16", "mesh64"],
+    ap.add_argument("--case", choices=["adjoint16", "mesh64", "batch4096", "ecf4096", "wecf64"],
                     help="run one untimed workload for an ncu capture (no JSON line)")
     args = ap.parse_args()
     if args.case:

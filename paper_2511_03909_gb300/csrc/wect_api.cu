@@ -966,7 +966,6 @@ static wect_status wecf_impl(wect_complex c, const double *filters, int m, int T
     if ((s = ensure_common_ws(c->ws, T))) return s;
     const int64_t total = (int64_t)m * c->nv;
     CK(c->ws.bins.ensure((size_t)total), "alloc bins");
-    KL(launch_finite_check(filters, total, c->d_status, kStatusBadIndex, st), "finite_check");
     const bool dflt = range_is_default(lo, hi);
     if (dflt) {
         // the paper's M is the largest |f| over all m filters
@@ -974,10 +973,13 @@ static wect_status wecf_impl(wect_complex c, const double *filters, int m, int T
         KL(launch_max_abs_f64(filters, total, 1, 0, c->ws.M.p, st), "max_abs");
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
-    KL(launch_filter_bins(filters, total, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, st), "filter_bins");
+    // exact bins of every filter value, and the finite check of the filters
+    KL(launch_filter_bins(filters, total, c->ws.range.p, c->ws.beta.p, T, c->ws.bins.p, c->d_status, kStatusBadIndex,
+                          st),
+       "filter_bins");
     CK(cudaMemsetAsync(out, 0, (size_t)m * T * sizeof(int64_t), st), "memset");
     if (c->kind == 0) {
-        KL(launch_cubical_ecf(c->n, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0,
+        KL(launch_cubical_ecf(c->n, c->d_grid, c->ws.bins.p, T, weighted ? 1 : 0, c->climit >> c->n,
                               reinterpret_cast<unsigned long long *>(out), c->nv, m, st),
            "cubical_ecf");
     } else {

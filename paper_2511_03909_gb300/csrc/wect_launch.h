@@ -92,9 +92,9 @@ cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size
 size_t cubical_bwd_rsum_smem(int n, int d, int T, int R);
 // ECF kernels for nf filters: bins [nf][nv], out [nf][T] (blockIdx.y = filter).
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
-                               unsigned long long *out, int64_t nv, int nf, cudaStream_t st);
+                               int64_t wbound, unsigned long long *out, int64_t nv, int nf, cudaStream_t st);
 cudaError_t launch_filter_bins(const double *f, int64_t nv, const double *range, const double *beta, int T,
-                               uint16_t *bins, cudaStream_t st);
+                               uint16_t *bins, int *status, int flag, cudaStream_t st);
 cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
                                 cudaStream_t st);
 
