@@ -986,8 +986,8 @@ static wect_status wecf_impl(wect_complex c, const double *filters, int m, int T
         for (int i = 0; i <= c->max_dim; ++i) {
             if (c->counts[i] == 0) continue;
             KL(launch_simplex_ecf(i == 0 ? nullptr : c->d_simp[i], c->d_sw[i], c->counts[i], i + 1, (i & 1) ? -1 : 1,
-                                  weighted ? 1 : 0, c->ws.bins.p, T, reinterpret_cast<unsigned long long *>(out), c->nv,
-                                  m, st),
+                                  weighted ? 1 : 0, c->climit, c->ws.bins.p, T,
+                                  reinterpret_cast<unsigned long long *>(out), c->nv, m, st),
                "simplex_ecf");
         }
     }

@@ -134,8 +134,8 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
                                   uint16_t *bins, unsigned long long *Iacc, float *grad, double scale,
                                   cudaStream_t st);
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
-                               const uint16_t *bins, int T, unsigned long long *out, int64_t nv, int nf,
-                               cudaStream_t st);
+                               int64_t wbound, const uint16_t *bins, int T, unsigned long long *out, int64_t nv,
+                               int nf, cudaStream_t st);
 
 // common
 cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const unsigned long long *Mbits, int T,

@@ -8,6 +8,9 @@
 // red.shared of a warp hits 32 distinct banks), flushed into the int64 output.
 #include <climits>
 
+#include <cmath>
+#include <type_traits>
+
 #include "wect_device.cuh"
 #include "wect_launch.h"
 
@@ -622,25 +625,39 @@ __global__ void i128_to_grad_kernel(const unsigned long long *Iacc, int64_t nv, 
         grad[v] = (float)(i128_to_double((int64_t)Iacc[2 * v + 1], Iacc[2 * v]) * scale);
 }
 
-template <int M>
-__global__ void simplex_ecf_kernel(const int32_t *simp, const int64_t *sw, int64_t k, int sign, int weighted,
-                                   const uint16_t *bins, int T, unsigned long long *out, int64_t nv)
+// WECF scatter of one list of M-vertex simplices for caller filters (Algorithm 1 with the vertex
+// filter's bins): each simplex's bin is the max of its vertex bins (Eq. "msi"), its signed
+// weight (or +-1) goes to a per-block histogram (int32, or int64 with H64) flushed once into
+// the int64 output, or with GHIST straight to the output.  blockIdx.y selects the filter.
+template <int M, bool H64, bool GHIST>
+__global__ void __launch_bounds__(256) simplex_ecf_kernel(const int32_t *simp, const int64_t *sw, int64_t k, int sign,
+                                                          int weighted, const uint16_t *bins, int T,
+                                                          unsigned long long *out, int64_t nv)
 {
+    using H = typename std::conditional<H64, unsigned long long, int>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    long long *h = reinterpret_cast<long long *>(smem);
+    H *h = reinterpret_cast<H *>(smem);
     bins += (int64_t)blockIdx.y * nv;       // filter blockIdx.y of [m][nv] bins, row of [m][T] out
     out += (int64_t)blockIdx.y * T;
-    for (int i = threadIdx.x; i < T; i += blockDim.x) h[i] = 0;
-    __syncthreads();
+    if (!GHIST) {
+        for (int i = threadIdx.x; i < T; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+    }
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < k; b += (int64_t)gridDim.x * blockDim.x) {
         int bin = 0;
+#pragma unroll
         for (int j = 0; j < M; ++j) bin = max(bin, (int)bins[(M == 1) ? b : simp[b * M + j]]);
         const long long w = weighted ? (long long)sw[b] : 1ll;
-        atomicAdd(reinterpret_cast<unsigned long long *>(&h[bin]), (unsigned long long)(sign > 0 ? w : -w));
+        const long long v = sign > 0 ? w : -w;
+        if (GHIST) atomicAdd(out + bin, (unsigned long long)v);
+        else if (H64) atomicAdd(&h[bin], (unsigned long long)v);
+        else atomicAdd(&h[bin], (int)v);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T; i += blockDim.x)
-        if (h[i]) atomicAdd(out + i, (unsigned long long)h[i]);
+    if (!GHIST) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < T; i += blockDim.x)
+            if (h[i]) atomicAdd(out + i, (unsigned long long)(long long)h[i]);
+    }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -843,28 +860,58 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
     return cudaGetLastError();
 }
 
+template <int M, bool H, bool G>
+static cudaError_t launch_simplex_ecf_t(dim3 g, size_t sm, const int32_t *simp, const int64_t *sw, int64_t k, int sign,
+                                        int weighted, const uint16_t *bins, int T, unsigned long long *out, int64_t nv,
+                                        cudaStream_t st)
+{
+    if (sm > 48u * 1024u) {
+        cudaError_t e = cudaFuncSetAttribute(simplex_ecf_kernel<M, H, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    simplex_ecf_kernel<M, H, G><<<g, 256, sm, st>>>(simp, sw, k, sign, weighted, bins, T, out, nv);
+    return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t launch_simplex_ecf_m(bool h64, bool ghist, dim3 g, size_t sm, const int32_t *simp,
+                                        const int64_t *sw, int64_t k, int sign, int weighted, const uint16_t *bins,
+                                        int T, unsigned long long *out, int64_t nv, cudaStream_t st)
+{
+    if (ghist) return launch_simplex_ecf_t<M, true, true>(g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    if (h64) return launch_simplex_ecf_t<M, true, false>(g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    return launch_simplex_ecf_t<M, false, false>(g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+}
+
+// Signed scatter of one simplex list for m filters: int32 shared histograms when enough blocks
+// keep each block's sum of |weight| (at most wbound per simplex) below 2^30, int64 otherwise,
+// global atomics when the histogram does not fit in shared memory.
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
-                               const uint16_t *bins, int T, unsigned long long *out, int64_t nv, int nf,
-                               cudaStream_t st)
+                               int64_t wbound, const uint16_t *bins, int T, unsigned long long *out, int64_t nv,
+                               int nf, cudaStream_t st)
 {
     if (k <= 0) return cudaSuccess;
-    const dim3 g((unsigned)std::min<int64_t>((k + 255) / 256, std::max(8, 1024 / std::max(nf, 1))), (unsigned)nf);
-    const size_t sm = (size_t)T * 8u;
-    cudaError_t e = cudaSuccess;
-#define SE(MM)                                                                                              \
-    do {                                                                                                    \
-        e = cudaFuncSetAttribute(simplex_ecf_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e == cudaSuccess) simplex_ecf_kernel<MM><<<g, 256, sm, st>>>(simp, sw, k, sign, weighted, bins, T, out, nv); \
-    } while (0)
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int64_t maxblocks = (k + 255) / 256;
+    const double wb = weighted ? (double)std::max<int64_t>(wbound, 1) : 1.0;
+    const double need = std::ceil((double)k * wb / 1073741824.0) + 1.0;
+    const bool h64 = need > (double)maxblocks;
+    size_t sm = (size_t)T * (h64 ? 8u : 4u);
+    const bool ghist = sm + 1024 > (size_t)optin;
+    if (ghist) sm = 0;
+    int64_t per = std::max<int64_t>(1, (int64_t)std::max(sms, 1) * 4 / std::max(nf, 1));
+    if (!h64) per = std::max<int64_t>(per, (int64_t)need);
+    const dim3 g((unsigned)std::min<int64_t>(maxblocks, per), (unsigned)nf);
     switch (m) {
-    case 1: SE(1); break;
-    case 2: SE(2); break;
-    case 3: SE(3); break;
-    default: SE(4); break;
+    case 1: return launch_simplex_ecf_m<1>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    case 2: return launch_simplex_ecf_m<2>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    case 3: return launch_simplex_ecf_m<3>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    default: return launch_simplex_ecf_m<4>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
     }
-#undef SE
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
 }
 
 }  // namespace wect

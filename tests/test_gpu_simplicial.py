@@ -112,6 +112,27 @@ def test_ecf_simplicial(P, oracle):
         assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("T", [2, 1000, 30000, 60000])
+def test_ecf_simplicial_histogram_modes(P, oracle, T):
+    """Per-block int32 histograms, int64 ones (f32 weights at 2^-24), and global atomics once T
+    no longer fits shared memory; values on the thresholds."""
+    cx = S.random_simplicial(300, 3, 900, 700, seed=17)
+    rng = np.random.default_rng(T)
+    beta = oracle.beta(T, -1.5, 1.5)
+    f = rng.uniform(-1.7, 1.7, cx.nv)
+    f[: min(cx.nv, T) // 2] = rng.choice(beta, size=min(cx.nv, T) // 2)
+    for kind in ("u8", "f32"):
+        w = cx.weights if kind == "u8" else rng.random(cx.nv, dtype=np.float32) * 3
+        h = P.SimplicialComplex(cuda(cx.coords), [cuda(x) for x in cx.simplices], cuda(w),
+                                frac_bits=24 if kind == "f32" else 0)
+        vw = w.astype(np.int64) if kind == "u8" else oracle.to_fixed(w, 24)
+        for weighted in (False, True):
+            got = h.ecf(cuda(f), T, -1.5, 1.5, weighted=weighted).cpu().numpy()
+            ws = oracle.simplicial_weights(cx.simplices, vw, "max" if weighted else "one")
+            ref = oracle.wecf_simplicial(f, cx.simplices, ws, T, -1.5, 1.5)[0]
+            assert np.array_equal(got, ref), (kind, weighted)
+
+
 def test_bad_indices_rejected(P):
     X = np.zeros((4, 2))
     E = np.array([[0, 1], [2, 7]], dtype=np.int32)
