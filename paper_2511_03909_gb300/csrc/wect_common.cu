@@ -126,6 +126,44 @@ __global__ void scan_rows_kernel(unsigned long long *data, int64_t rows, int T)
     }
 }
 
+// Long rows (T in the thousands): one block per row.  Each thread sums a contiguous piece of
+// the row, the block scans the piece sums (warp shuffles, then the warp totals), and each thread
+// rewrites its piece as running sums from its exclusive prefix.  A warp per row would walk T / 32
+// dependent steps.
+__global__ void __launch_bounds__(1024) scan_rows_block_kernel(unsigned long long *data, int T)
+{
+    __shared__ long long wsum[32];
+    long long *r = reinterpret_cast<long long *>(data) + (int64_t)blockIdx.x * T;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (T + blockDim.x - 1) / blockDim.x;
+    const int q0 = min(T, (int)threadIdx.x * per), q1 = min(T, q0 + per);
+    long long s = 0;
+    for (int q = q0; q < q1; ++q) s += r[q];
+    long long v = s;                                  // inclusive scan of the piece sums
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += u;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        long long w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += u;
+        }
+        if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    long long run = v - s + (wid > 0 ? wsum[wid - 1] : 0);   // exclusive prefix of the piece
+    for (int q = q0; q < q1; ++q) {
+        run += r[q];
+        r[q] = run;
+    }
+}
+
 // Suffix sums S[q] = sum_{q' >= q} G[q'] of each row (the adjoint of the prefix scan).  The
 // adjoint later sums S over up to d directions in int64: entries with |S| > smax flag overflow.
 __global__ void suffix_rows_kernel(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status)
@@ -307,6 +345,13 @@ cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int 
 
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st)
 {
+    if (rows <= 0) return cudaSuccess;
+    if (T >= 1024 && rows <= 65535) {
+        // a block of up to 1024 threads per row, about 8 entries per thread
+        const int threads = std::min(1024, ((T + 7) / 8 + 31) / 32 * 32);
+        scan_rows_block_kernel<<<(unsigned)rows, threads, 0, st>>>(data, T);
+        return cudaGetLastError();
+    }
     const int wpb = 8;
     scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(data, rows, T);
     return cudaGetLastError();

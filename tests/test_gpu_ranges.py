@@ -57,3 +57,20 @@ def test_simplicial_forward_and_adjoint_narrow_ranges(P, oracle, r):
     g = h.backward(cuda(dirs), T, lo, hi, cuda(G), 2.0 ** -30).cpu().numpy()
     gref = oracle.wect_backward_simplicial(cx.coords, vw, cx.simplices, dirs, T, lo, hi, G, 2.0 ** -30)
     assert np.array_equal(g, gref)
+
+
+def test_long_threshold_rows(P, oracle):
+    """T = 1500: the prefix scan over thresholds takes one block per row."""
+    dims = [45, 38]
+    w = S.uniform_u8_grid(dims, seed=51)
+    dirs = S.circle_directions(20)
+    cx = P.CubicalComplex(cuda(w))
+    got = cx.wect(cuda(dirs), 1500, -1.5, 1.5).cpu().numpy()
+    ref = oracle.wect_cubical(dims, w.ravel(), dirs, 1500, -1.5, 1.5)
+    assert np.array_equal(got, ref)
+    sc = S.random_simplicial(150, 2, 400, 200, seed=52)
+    h = P.SimplicialComplex(cuda(sc.coords), [cuda(x) for x in sc.simplices], cuda(sc.weights))
+    got = h.wect(cuda(dirs), 1500, -1.5, 1.5).cpu().numpy()
+    vw = sc.weights.astype(np.int64)
+    ref = oracle.wect_simplicial(sc.coords, sc.simplices, oracle.simplicial_weights(sc.simplices, vw), dirs, 1500, -1.5, 1.5)
+    assert np.array_equal(got, ref)
