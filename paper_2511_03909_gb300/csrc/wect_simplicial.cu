@@ -293,39 +293,69 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     // CTA-uniform steps of nw * VG vertices (so that the periodic flush is a block-wide barrier),
     // at most P.flush_every steps between flushes
     const int64_t cstep = (int64_t)nw * VG;
+    const int nvm1 = (int)(nv - 1);                  // vertex ids are int32
     int since = 0;
     for (int64_t base = (int64_t)blockIdx.x * cstep; base < nv; base += (int64_t)gridDim.x * cstep) {
-        const int64_t v0 = base + (int64_t)wid * VG;
+        const int v0 = (int)(base + (int64_t)wid * VG);
         float x[VG][3];
         int2 w[VG];
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
-            const int64_t v = min(v0 + g, nv - 1);
+            const int v = min(v0 + g, nvm1);
 #pragma unroll
-            for (int a = 0; a < N; ++a) x[g][a] = __ldg(xf + v * N + a);
-            w[g] = (v0 + g < nv) ? __ldg(P.swp + v) : make_int2(0, 0);
+            for (int a = 0; a < N; ++a) x[g][a] = __ldg(xf + (int64_t)v * N + a);
+            w[g] = (v0 + g <= nvm1) ? __ldg(P.swp + v) : make_int2(0, 0);
         }
+        // branch-free pass: candidate bins, stores and scatters; undecided bins are only marked
+        int bc[VG];
+        uint32_t pend = 0;
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
-            const int64_t v = min(v0 + g, nv - 1);
             float u = t0.w;
 #pragma unroll
             for (int a = N - 1; a >= 0; --a) u = __fmaf_rn(x[g][a], Af[a], u);
             const int tlo = __float_as_int(__fadd_ru(__fsub_rd(u, eta), kMagic));
             const int thi = __float_as_int(__fadd_ru(__fadd_ru(u, eta), kMagic));
-            int b = clamp_bin(thi, 0, T);
-            if (tlo != thi) {
-                double xd[3] = {0.0, 0.0, 0.0};
-                for (int a = 0; a < N; ++a) xd[a] = coords[v * N + a];
-                const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
-                b = exact_bin_from(h, beta, T, b);
-            }
+            const int b = clamp_bin(thi, 0, T);
+            bc[g] = b;
+            pend |= (tlo != thi ? 1u : 0u) << g;
             // every column gets a valid bin (a padding column carries direction d - 1's), so the
             // gathers never read an unwritten entry
-            if (v0 + g < nv) bins[v * 32 + lane] = (uint16_t)b;
+            if (v0 + g <= nvm1) bins[(int64_t)(v0 + g) * 32 + lane] = (uint16_t)b;
             const uint32_t addr = histLane + (uint32_t)b * 128u;
             red_shared_add(addr, w[g].x);
             if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+        }
+        // undecided bins: the exact float64 bin, and the contribution moved if it differs (the
+        // entry it leaves received it above, so the low plane stays non-negative)
+        if (__any_sync(0xffffffffu, pend != 0)) {
+            while (pend) {
+                const int g = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int v = min(v0 + g, nvm1);
+                double xd[3] = {0.0, 0.0, 0.0};
+                for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
+                const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
+                int bg = 0, wx = 0, wy = 0;
+#pragma unroll
+                for (int k = 0; k < VG; ++k)
+                    if (k == g) {
+                        bg = bc[k];
+                        wx = w[k].x;
+                        wy = w[k].y;
+                    }
+                const int be = exact_bin_from(h, beta, T, bg);
+                if (be != bg) {
+                    if (v0 + g <= nvm1) bins[(int64_t)(v0 + g) * 32 + lane] = (uint16_t)be;
+                    const uint32_t at = histLane + (uint32_t)bg * 128u, ae = histLane + (uint32_t)be * 128u;
+                    red_shared_add(at, -wx);
+                    red_shared_add(ae, wx);
+                    if (NSPLIT == 2) {
+                        red_shared_add(at + HOFF, -wy);
+                        red_shared_add(ae + HOFF, wy);
+                    }
+                }
+            }
         }
         if (++since >= P.flush_every) {
             simplex_flush<NSPLIT>(hist, T, P.dtile, d, P.out);
