@@ -177,7 +177,8 @@ struct DBuf {
 struct Workspace {
     DBuf<double> range;           // [6]: lo, hi, step, max|x_0..2|
     DBuf<double> beta;            // [T]
-    DBuf<unsigned long long> M;   // [2]: max-abs bits, float lower-bound scratch
+    DBuf<unsigned long long> M;   // [2]: max-abs bits, scratch (argmax key of the default range)
+    DBuf<int> cand;               // default range of a simplicial complex: {count, L, Smax, 0, candidates}
     DBuf<int> counter;            // work-queue head
     DBuf<int> perm, octb;         // octant grouping of the directions
     DBuf<uint16_t> bins;          // vertex bins
@@ -195,7 +196,7 @@ struct Workspace {
     int n_items = 0, n_items_bwd = 0;
     void release()
     {
-        range.release(); beta.release(); M.release(); counter.release(); perm.release(); octb.release();
+        range.release(); beta.release(); M.release(); cand.release(); counter.release(); perm.release(); octb.release();
         bins.release(); dtab.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
         items_bwd.release();
     }
@@ -865,10 +866,11 @@ static wect_status simplicial_range(wect_complex c, const double *dirs, int d, i
 {
     const bool dflt = range_is_default(lo, hi);
     if (dflt) {
+        CK(c->ws.cand.ensure((size_t)c->nv + 4), "alloc range candidates");
         CK(cudaMemsetAsync(c->ws.M.p, 0, 2 * sizeof(unsigned long long), st), "memset");
-        KL(launch_simplicial_max_abs(c->n, c->d_coords, c->d_xf, c->nv, dirs, d, c->ws.M.p,
-                                     reinterpret_cast<float *>(c->ws.M.p + 1), st), "max_abs");
-        g_launches++;    // two passes
+        KL(launch_simplicial_max_abs(c->n, c->d_coords, c->d_xf, c->nv, dirs, d, c->ws.M.p, c->ws.M.p + 1,
+                                     c->ws.cand.p, st), "max_abs");
+        g_launches += 3;    // four kernels
     }
     KL(launch_setup_range_beta(lo, hi, dflt ? 1 : 0, c->ws.M.p, T, c->ws.range.p, c->ws.beta.p, st), "setup_range_beta");
     CK(c->ws.dtab.ensure((size_t)d * 8), "alloc filter table");

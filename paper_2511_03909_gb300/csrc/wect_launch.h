@@ -125,7 +125,8 @@ cudaError_t launch_simplex_fwd_staged(int nsplit, const SimplexFwdArgs &a, int g
 size_t simplex_fwd_staged_smem(int nsplit, int T, int Dt);
 size_t simplex_fwd_smem(int nsplit, int T, int Dt);
 cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
-                                      int d, unsigned long long *Mbits, float *Lscratch, cudaStream_t st);
+                                      int d, unsigned long long *Mbits, unsigned long long *key, int *cand,
+                                      cudaStream_t st);
 cudaError_t launch_simplex_weights_max(const int32_t *simp, int64_t k, int m, const int64_t *vw, int64_t *sw,
                                        cudaStream_t st);
 cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, int64_t nv, const int32_t *const *simp,

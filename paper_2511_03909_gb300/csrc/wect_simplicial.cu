@@ -552,30 +552,139 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(
 
 // ------------------------------------------------------------------ default range
 
-// Pass 1: a float32 lower bound L on max |h| (|h~| - E); pass 2: exact float64 |h| of every
-// (vertex, direction) whose float32 upper bound reaches L.  Each thread keeps one vertex and
-// walks the directions, staged in shared memory kMaxAbsDirs at a time.
 constexpr int kMaxAbsDirs = 1024;
 
-template <int N, int PASS>
-__global__ void __launch_bounds__(256) simplicial_max_abs_kernel(const double *__restrict__ coords,
-                                                                 const float *__restrict__ xf, int64_t nv,
+// The default range M = max over directions p and vertices v of |h_p(v)| (Section 3), exactly in
+// float64, without evaluating every (p, v):
+//   1. the vertex v* of largest norm (float32, argmax only);
+//   2. L = max_p |h_p(v*)| in float64, a lower bound of M, and Smax >= max_p |s_p|;
+//   3. the candidates: vertices with |x| Smax (rounded up, with margin for the float32 copy of x
+//      and the float64 roundings of h) >= L; no other vertex can reach M (Cauchy-Schwarz);
+//   4. for each candidate and direction, a float32 height with an error bound E, and the float64
+//      height wherever |h| + E >= L.
+// Typical point sets leave a handful of candidates; in the worst case (every vertex at the same
+// norm) step 4 covers all vertices, as a plain screened pass would.
+template <int N>
+__global__ void __launch_bounds__(256) vertex_norm_argmax_kernel(const float *__restrict__ xf, int64_t nv,
+                                                                 unsigned long long *key)
+{
+    unsigned long long best = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const float x = __ldg(xf + v * N + a);
+            s = __fmaf_rn(x, x, s);
+        }
+        best = max(best, ((unsigned long long)__float_as_uint(s) << 32) | (unsigned long long)(uint32_t)v);
+    }
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, off));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+// One block: L and Smax (step 2).  M starts at L; cand = {count, L rounded down, Smax, 0, list}.
+template <int N>
+__global__ void __launch_bounds__(256) range_lower_bound_kernel(const double *__restrict__ coords,
+                                                                const double *__restrict__ dirs, int d,
+                                                                const unsigned long long *key,
+                                                                unsigned long long *Mbits, int *cand)
+{
+    __shared__ double sb[32];
+    __shared__ float ss[32];
+    const int v = (int)(uint32_t)(*key & 0xffffffffull);
+    double xd[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
+    double best = 0.0;
+    float smax = 0.f;
+    for (int p = threadIdx.x; p < d; p += blockDim.x) {
+        best = fmax(best, fabs(height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)p * N)));
+        float s2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const float sa = __double2float_ru(fabs(dirs[(int64_t)p * N + a]));
+            s2 = __fmaf_ru(sa, sa, s2);
+        }
+        smax = fmaxf(smax, __fsqrt_ru(s2));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        best = fmax(best, __shfl_down_sync(0xffffffffu, best, off));
+        smax = fmaxf(smax, __shfl_down_sync(0xffffffffu, smax, off));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        sb[wid] = best;
+        ss[wid] = smax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            best = fmax(best, sb[w]);
+            smax = fmaxf(smax, ss[w]);
+        }
+        atomicMax(Mbits, (unsigned long long)__double_as_longlong(best));
+        cand[1] = __float_as_int(__double2float_rd(best));
+        cand[2] = __float_as_int(smax);
+    }
+}
+
+// Step 3: append every vertex whose norm bound reaches L to the list (warp-aggregated).
+template <int N>
+__global__ void __launch_bounds__(256) range_candidates_kernel(const float *__restrict__ xf, int64_t nv, int *cand)
+{
+    const float L = __int_as_float(cand[1]), Smax = __int_as_float(cand[2]);
+    const int lane = threadIdx.x & 31;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < nv;
+         v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + lane;
+        bool c = false;
+        if (v < nv) {
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const float x = fabsf(__ldg(xf + v * N + a));
+                s = __fmaf_ru(x, x, s);
+            }
+            // |x| <= |x~| (1 + 2^-24) for the float32 copy x~; the float64 height rounds by far
+            // less than the 2^-20 margin
+            const float ub = __fadd_ru(__fmul_ru(__fmul_ru(__fsqrt_ru(s), Smax), 1.0f + 0x1p-20f), 0x1p-100f);
+            c = ub >= L;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, c);
+        if (m) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&cand[0], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (c) cand[4 + base + __popc(m & ((1u << lane) - 1u))] = (int)v;
+        }
+    }
+}
+
+// Step 4: warps over candidates, lanes over a shared-memory chunk of directions.
+template <int N>
+__global__ void __launch_bounds__(256) max_abs_candidates_kernel(const double *__restrict__ coords,
+                                                                 const float *__restrict__ xf,
                                                                  const double *__restrict__ dirs, int d,
-                                                                 unsigned long long *Mbits, unsigned int *Lbits)
+                                                                 const int *__restrict__ cand,
+                                                                 unsigned long long *Mbits)
 {
     __shared__ float sd[kMaxAbsDirs][N];
-    const float L = (PASS == 2) ? __uint_as_float(*Lbits) : 0.f;
-    unsigned int best = 0;
+    const int count = cand[0];
+    const float L = __int_as_float(cand[1]);
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int p0 = 0; p0 < d; p0 += kMaxAbsDirs) {
         const int np = min(kMaxAbsDirs, d - p0);
         __syncthreads();
         for (int i = threadIdx.x; i < np * N; i += blockDim.x) sd[i / N][i % N] = __double2float_rn(dirs[(int64_t)p0 * N + i]);
         __syncthreads();
-        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t ci = gw; ci < count; ci += nw) {
+            const int v = cand[4 + ci];
             float x[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int a = 0; a < N; ++a) x[a] = __ldg(xf + v * N + a);
-            for (int j = 0; j < np; ++j) {
+            for (int a = 0; a < N; ++a) x[a] = __ldg(xf + (int64_t)v * N + a);
+            for (int j = lane; j < np; j += 32) {
                 float h = 0.f, mag = 0.f;
 #pragma unroll
                 for (int a = N - 1; a >= 0; --a) {
@@ -583,21 +692,14 @@ __global__ void __launch_bounds__(256) simplicial_max_abs_kernel(const double *_
                     mag = __fmaf_ru(fabsf(x[a]), fabsf(sd[j][a]), mag);
                 }
                 const float E = __fmul_ru(mag, 0x1p-19f) + 0x1p-126f;
-                if (PASS == 1) {
-                    const float lb = __fsub_rd(fabsf(h), E);
-                    if (lb > 0.f) best = max(best, __float_as_uint(lb));
-                } else if (__fadd_ru(fabsf(h), E) >= L) {
+                if (__fadd_ru(fabsf(h), E) >= L) {
                     double xd[3] = {0.0, 0.0, 0.0};
-                    for (int a = 0; a < N; ++a) xd[a] = coords[v * N + a];
+                    for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
                     const double hd = fabs(height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)(p0 + j) * N));
                     atomicMax(Mbits, (unsigned long long)__double_as_longlong(hd));
                 }
             }
         }
-    }
-    if (PASS == 1) {
-        for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, off));
-        if ((threadIdx.x & 31) == 0) atomicMax(Lbits, best);
     }
 }
 
@@ -830,16 +932,19 @@ cudaError_t launch_simplex_fwd_staged(int nsplit, const SimplexFwdArgs &a, int g
 }
 
 cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
-                                      int d, unsigned long long *Mbits, float *Lscratch, cudaStream_t st)
+                                      int d, unsigned long long *Mbits, unsigned long long *key, int *cand,
+                                      cudaStream_t st)
 {
-    unsigned int *Lbits = reinterpret_cast<unsigned int *>(Lscratch);
+    if (nv <= 0) return cudaSuccess;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 152 * 8));
-    cudaError_t e = cudaMemsetAsync(Lbits, 0, sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(cand, 0, 4 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-#define MA(NN)                                                                                      \
-    do {                                                                                            \
-        simplicial_max_abs_kernel<NN, 1><<<g, 256, 0, st>>>(coords, xf, nv, dirs, d, Mbits, Lbits); \
-        simplicial_max_abs_kernel<NN, 2><<<g, 256, 0, st>>>(coords, xf, nv, dirs, d, Mbits, Lbits); \
+#define MA(NN)                                                                                          \
+    do {                                                                                                \
+        vertex_norm_argmax_kernel<NN><<<g, 256, 0, st>>>(xf, nv, key);                                 \
+        range_lower_bound_kernel<NN><<<1, 256, 0, st>>>(coords, dirs, d, key, Mbits, cand);            \
+        range_candidates_kernel<NN><<<g, 256, 0, st>>>(xf, nv, cand);                                  \
+        max_abs_candidates_kernel<NN><<<g, 256, 0, st>>>(coords, xf, dirs, d, cand, Mbits);            \
     } while (0)
     if (n == 1) MA(1);
     else if (n == 2) MA(2);

@@ -74,3 +74,34 @@ def test_long_threshold_rows(P, oracle):
     vw = sc.weights.astype(np.int64)
     ref = oracle.wect_simplicial(sc.coords, sc.simplices, oracle.simplicial_weights(sc.simplices, vw), dirs, 1500, -1.5, 1.5)
     assert np.array_equal(got, ref)
+
+
+def _chain_complex(X):
+    """Vertices X with edges between consecutive points (a path)."""
+    nv = X.shape[0]
+    edges = np.stack([np.arange(nv - 1), np.arange(1, nv)], axis=1).astype(np.int32)
+    return [edges]
+
+
+@pytest.mark.parametrize("case", ["circle", "origin", "outliers3d"])
+def test_simplicial_default_range_candidates(P, oracle, case):
+    """The default range M = max |h| over all vertices and directions: every vertex of a circle is
+    a candidate, a complex at the origin has M = 0, and far outliers leave a few candidates."""
+    rng = np.random.default_rng(61)
+    if case == "circle":
+        t = rng.uniform(0, 2 * np.pi, 3000)
+        X = np.stack([np.cos(t), np.sin(t)], axis=1)
+        dirs = S.random_directions(300, 2, 62)
+    elif case == "origin":
+        X = np.zeros((50, 2))
+        dirs = S.circle_directions(16)
+    else:
+        X = rng.uniform(-1, 1, (5000, 3))
+        X[[7, 123, 4000]] = [[9.0, -3.0, 2.0], [-8.5, 4.0, -4.0], [3.0, 9.25, 1.0]]
+        dirs = S.fibonacci_directions(200)
+    lists = _chain_complex(X)
+    w = rng.integers(0, 256, X.shape[0]).astype(np.uint8)
+    h = P.SimplicialComplex(cuda(X), [cuda(x) for x in lists], cuda(w))
+    got = h.wect(cuda(dirs), 33).cpu().numpy()
+    ref = oracle.wect_simplicial(X, lists, oracle.simplicial_weights(lists, w.astype(np.int64)), dirs, 33)
+    assert np.array_equal(got, ref)
