@@ -294,18 +294,33 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     // at most P.flush_every steps between flushes
     const int64_t cstep = (int64_t)nw * VG;
     const int nvm1 = (int)(nv - 1);                  // vertex ids are int32
+    const int64_t gstep = (int64_t)gridDim.x * cstep;
+    // coordinates and weights of the warp's next group, loaded one step ahead
+    float xn[VG][3];
+    int2 wn[VG];
+    auto load_group = [&](int64_t base) {
+        const int v0 = (int)(base + (int64_t)wid * VG);
+#pragma unroll
+        for (int g = 0; g < VG; ++g) {
+            const int v = min(v0 + g, nvm1);
+#pragma unroll
+            for (int a = 0; a < N; ++a) xn[g][a] = __ldg(xf + (int64_t)v * N + a);
+            wn[g] = (v0 + g <= nvm1) ? __ldg(P.swp + v) : make_int2(0, 0);
+        }
+    };
+    if ((int64_t)blockIdx.x * cstep < nv) load_group((int64_t)blockIdx.x * cstep);
     int since = 0;
-    for (int64_t base = (int64_t)blockIdx.x * cstep; base < nv; base += (int64_t)gridDim.x * cstep) {
+    for (int64_t base = (int64_t)blockIdx.x * cstep; base < nv; base += gstep) {
         const int v0 = (int)(base + (int64_t)wid * VG);
         float x[VG][3];
         int2 w[VG];
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
-            const int v = min(v0 + g, nvm1);
 #pragma unroll
-            for (int a = 0; a < N; ++a) x[g][a] = __ldg(xf + (int64_t)v * N + a);
-            w[g] = (v0 + g <= nvm1) ? __ldg(P.swp + v) : make_int2(0, 0);
+            for (int a = 0; a < N; ++a) x[g][a] = xn[g][a];
+            w[g] = wn[g];
         }
+        if (base + gstep < nv) load_group(base + gstep);
         // branch-free pass: candidate bins, stores and scatters; undecided bins are only marked
         int bc[VG];
         uint32_t pend = 0;
