@@ -258,6 +258,9 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
     }
     F2 k02 = f2_pack(k0, k0);
     const F2 two2 = f2_pack(2.0f, 2.0f);
+    // four blocks of U vertices per trip: the scheduler overlaps one block's shared-memory
+    // scatter with the next block's filter arithmetic
+#pragma unroll 4
     for (int i0 = 0; i0 < LU; i0 += U) {
         int cv[DPL][U], hv[DPL][U];
 #pragma unroll

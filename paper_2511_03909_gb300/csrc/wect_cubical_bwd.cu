@@ -127,6 +127,16 @@ __device__ __forceinline__ int rsum_group(uint32_t e, int gi, bool clampg, F2 KA
     return bad;
 }
 
+// An octant sum as two int32 halves, value = hi * 2^32 + lo with lo the signed low word (so hi
+// is the high word plus one when lo < 0).  The routing kernel then multiplies each half by its
+// small coefficient with one 32 x 32 -> 64 multiply-add.  |value| < 2^63 / 3^n keeps hi in range.
+__device__ __forceinline__ void store_split(int64_t *p, long long v)
+{
+    const int lo = (int)(unsigned int)((unsigned long long)v & 0xffffffffull);
+    const int hi = (int)((v - (long long)lo) >> 32);
+    *reinterpret_cast<int2 *>(p) = make_int2(lo, hi);
+}
+
 template <int N>
 __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const CubicalBwdArgs P)
 {
@@ -277,8 +287,8 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
                         }
                     }
                 }
-                if (liveA) P.Rv[(int64_t)o * P.total_nv + voutA] = accA;
-                if (liveB) P.Rv[(int64_t)o * P.total_nv + voutA + 32] = accB;
+                if (liveA) store_split(P.Rv + (int64_t)o * P.total_nv + voutA, accA);
+                if (liveB) store_split(P.Rv + (int64_t)o * P.total_nv + voutA + 32, accB);
             }
         }
     }
@@ -340,6 +350,29 @@ __host__ __device__ constexpr uint32_t route_class_mask(int n, int o, int delta,
         if (in && (dim & 1) == par) m |= 1u << t;
     }
     return m;
+}
+
+// Cells of odd dimension among the 3^n neighbourhood cells, and the population count of a mask
+// (both for compile-time masks).
+__host__ __device__ constexpr uint32_t route_odd_mask(int n)
+{
+    uint32_t m = 0;
+    for (int t = 0; t < route_nb(n); ++t) {
+        int mul = 1, dim = 0;
+        for (int a = 0; a < n; ++a) {
+            dim += (t / mul) % 3 != 1;
+            mul *= 3;
+        }
+        if (dim & 1) m |= 1u << t;
+    }
+    return m;
+}
+
+__host__ __device__ constexpr int route_popcount(uint32_t m)
+{
+    int c = 0;
+    for (; m; m &= m - 1) ++c;
+    return c;
 }
 
 // Neighbourhood index of the corner v + delta * sg(o).
@@ -412,18 +445,26 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
     for (int t = 0; t < NB; ++t)
         if ((okm >> t) & 1u)
             if ((beat & route_cell_mask(N, t)) == 0) A |= 1u << t;
-    long long acc = 0;
+    // K = #(A & even & class) - #(A & odd & class) = #(X & class) - #(odd & class) with
+    // X = A ^ odd: one mask and one popcount per coefficient, the second count a constant
+    const uint32_t X = A ^ route_odd_mask(N);
+    // the octant sums are stored as (lo, hi) int32 halves: sum K * lo and K * hi separately
+    // (|K| <= 2^n, 4^n terms: both sums stay far inside int64), combined modulo 2^64 at the end
+    long long acc_lo = 0, acc_hi = 0;
 #pragma unroll
     for (int o = 0; o < NOCT; ++o) {
-        const long long *R = reinterpret_cast<const long long *>(P.Rv) + (int64_t)o * P.total_nv + gid;
+        const int2 *R = reinterpret_cast<const int2 *>(P.Rv) + (int64_t)o * P.total_nv + gid;
 #pragma unroll
         for (int dl = 0; dl < NOCT; ++dl) {
-            const int K = __popc(A & route_class_mask(N, o, dl, 0)) - __popc(A & route_class_mask(N, o, dl, 1));
+            const uint32_t cls = route_class_mask(N, o, dl, 0) | route_class_mask(N, o, dl, 1);
+            const int K = __popc(X & cls) - route_popcount(route_odd_mask(N) & cls);
             // K == 0 whenever the corner lies outside the grid (every cell of the class holds it)
-            const long long r = (K != 0) ? __ldg(R + off[route_corner(N, o, dl)]) : 0ll;
-            acc += (long long)K * r;
+            const int2 r = (K != 0) ? __ldg(R + off[route_corner(N, o, dl)]) : make_int2(0, 0);
+            acc_lo += (long long)K * r.x;
+            acc_hi += (long long)K * r.y;
         }
     }
+    const long long acc = (long long)(((unsigned long long)acc_hi << 32) + (unsigned long long)acc_lo);
     const double scale = P.scale_dev ? *P.scale_dev : P.scale;
     P.grad[gid] = (float)((double)acc * scale);
 }

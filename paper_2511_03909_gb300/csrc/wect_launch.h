@@ -38,7 +38,7 @@ struct CubicalBwdArgs {
     const int *octb;              // [2^n + 1] octant bounds in perm
     int R;
     const int64_t *S;             // suffix sums [count][d][T]
-    int64_t *Rv;                  // [2^n][total_nv] (octant-major planes)
+    int64_t *Rv;                  // [2^n][total_nv] octant sums (octant-major planes), as int32 halves
     float *grad;                  // [total_nv]
     int64_t v_begin, v_end;       // vertex range the routing kernel covers
     double scale;
