@@ -375,8 +375,8 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
 // Items for a set of grids: per complex, direction tiles x row chunks, largest first.  An item
 // never holds more than kflush vertices (the int32 histogram bound); whole=true keeps one chunk
 // per complex (the caller has checked that every complex fits).
-static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int kflush, int target_items,
-                                        bool whole)
+static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int T, int kflush,
+                                        int target_items, bool whole)
 {
     const int ntiles = (d + Dt - 1) / Dt;
     std::vector<std::pair<int64_t, WorkItem>> v;
@@ -389,6 +389,9 @@ static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int 
         if (!whole) {
             const double share = (double)g.rows / (double)std::max<int64_t>(total_rows, 1);
             chunks = (int)std::ceil(share * target_items / ntiles);
+            // no item smaller than 8x its histogram flush (T x Dt entries): rows * L0 >= 8 T
+            const int min_rows = (int)std::min<int64_t>(g.rows, (8ll * T + g.L[0] - 1) / std::max(1, g.L[0]));
+            chunks = std::min(chunks, std::max(1, g.rows / std::max(1, min_rows)));
             chunks = std::max(chunks, (g.rows + max_rows - 1) / max_rows);
             chunks = std::max(1, std::min(chunks, g.rows));
         }
@@ -854,7 +857,7 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
         gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
         gv[0].rows = rows;
         gv[0].nv = c->nv;
-        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, c->kflush, sh.grid, false);
+        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, T, c->kflush, sh.grid, false);
         if ((s = upload_items(c->ws, items, st))) return s;
         c->ws.items_key = key;
     }
@@ -1308,7 +1311,7 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
     direct = maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
     auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, direct ? 1 : 0);
     if (b->ws.items_key == key) return WECT_OK;
-    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, b->kflush, 4 * sh.grid, direct);
+    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, T, b->kflush, 4 * sh.grid, direct);
     wect_status s = upload_items(b->ws, items, st);
     if (s) return s;
     b->ws.items_key = key;
@@ -1398,7 +1401,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         starts.assign(b->count + 1, 0);
         for (int i = 0; i < b->count; ++i) {
             std::vector<GridDesc> one(1, b->h_grids[i]);
-            std::vector<WorkItem> it = make_items(one, d, sh.Dt, b->kflush, sh.grid, false);
+            std::vector<WorkItem> it = make_items(one, d, sh.Dt, T, b->kflush, sh.grid, false);
             for (auto &w : it) w.cx = i;
             starts[i] = (int)all.size();
             all.insert(all.end(), it.begin(), it.end());
