@@ -305,7 +305,8 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
 //     I_v = sum_o sum_delta K[o][delta] * Rv[o][v + delta * sg],
 //     K[o][delta] = #(A & even cells of the class) - #(A & odd cells of the class),
 // where the class of (o, delta) is the cells with e_a = sg_a on delta and e_a in {0, -sg_a}
-// off it.  That is 2^n x 2^n coalesced loads per vertex and no divergence.  Every partial sum is
+// off it (computed below with one mask and one popcount each).  That is 2^n x 2^n coalesced
+// loads per vertex and no divergence.  Every partial sum is
 // a signed sum over at most 3^n cells of sums over disjoint direction sets, so with
 // 3^n d max|S| < 2^63 (checked when the suffix table is built) int64 is exact.
 __host__ __device__ constexpr int route_nb(int n) { return n == 1 ? 3 : (n == 2 ? 9 : 27); }
