@@ -237,6 +237,22 @@ __global__ void weights_to_w32_kernel(const void *w, int64_t nv, int frac_bits, 
     }
 }
 
+// u8 weights (which never exceed the limit, at least 255): 16 per thread step, one 16-byte load
+// and four 16-byte stores, then the tail.  w is 16-byte aligned.
+__global__ void weights_u8_to_w32_kernel(const uint8_t *__restrict__ w, int64_t nv, int32_t *__restrict__ out)
+{
+    const int64_t n16 = nv >> 4, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(w) + i);
+        int4 *o = reinterpret_cast<int4 *>(out) + 4 * i;
+        const unsigned q[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            o[k] = make_int4((int)(q[k] & 255u), (int)((q[k] >> 8) & 255u), (int)((q[k] >> 16) & 255u), (int)(q[k] >> 24));
+    }
+    for (int64_t v = (n16 << 4) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) out[v] = w[v];
+}
+
 template <int WT>
 __global__ void weights_check_kernel(const void *w, int64_t nv, int frac_bits, int64_t limit, int *status)
 {
@@ -403,6 +419,11 @@ cudaError_t launch_weights_to_w32(int wt, const void *w, int64_t nv, int frac_bi
                                   int *status, cudaStream_t st)
 {
     const unsigned g = grid_for(nv, 256);
+    if (wt == WT_U8 && limit >= 255 && (reinterpret_cast<uintptr_t>(w) & 15u) == 0) {
+        weights_u8_to_w32_kernel<<<grid_for(std::max<int64_t>(nv >> 4, 1), 256), 256, 0, st>>>(
+            static_cast<const uint8_t *>(w), nv, out);
+        return cudaGetLastError();
+    }
     switch (wt) {
     case WT_U8: weights_to_w32_kernel<WT_U8><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
     case WT_I64: weights_to_w32_kernel<WT_I64><<<g, 256, 0, st>>>(w, nv, frac_bits, limit, out, status); break;
