@@ -213,7 +213,7 @@ cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bin
 {
     static const int sms = std::max(1, device_attr(cudaDevAttrMultiProcessorCount));
     static const size_t optin = (size_t)device_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin);
-    const int threads = T > 2048 ? 1024 : 256;
+    const int threads = T > 2048 ? 1024 : 512;
     const int64_t maxblocks = std::max<int64_t>(1, (nv + threads - 1) / threads);
     // blocks per filter that keep a block's sum of |weight| (2^n cells per vertex, each at most
     // wbound) below 2^30 in an int32 histogram
@@ -223,9 +223,9 @@ cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bin
     size_t sm = (size_t)T * (h64 ? 8u : 4u);
     const bool ghist = sm + 1024 > optin;
     if (ghist) sm = 0;
-    // 1024 threads per SM over all filters: four blocks of 256 for small T, one of 1024 when the
-    // flush of each block's T-entry histogram (global atomics) would cost more
-    int64_t per = std::max<int64_t>(1, (int64_t)sms * (1024 / threads) / std::max(nf, 1));
+    // over all filters: four blocks of 512 per SM (full occupancy) for small T, one of 1024 when
+    // the flush of each block's T-entry histogram (global atomics) would cost more
+    int64_t per = std::max<int64_t>(1, (int64_t)sms * (T > 2048 ? 1 : 4) / std::max(nf, 1));
     if (!h64) per = std::max<int64_t>(per, (int64_t)need);
     const dim3 blocks((unsigned)std::min<int64_t>(maxblocks, per), (unsigned)nf);
     if (n == 1) return launch_ecf_n<1>(weighted != 0, h64, ghist, blocks, threads, sm, grids, bins, T, out, st);
