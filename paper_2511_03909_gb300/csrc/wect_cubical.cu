@@ -108,6 +108,25 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int 
                                               unsigned long long *out)
 {
     const int hw = T * Dt;
+    if (blockDim.x % Dt == 0) {
+        // each thread keeps one column: no division and one perm load per thread
+        const int col = threadIdx.x % Dt, bstep = blockDim.x / Dt;
+        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
+        unsigned long long *orow = out + (int64_t)min(p, d - 1) * T;
+        for (int b = threadIdx.x / Dt; b < T; b += bstep) {
+            const int idx = b * Dt + col;
+            int64_t v;
+            if (NSPLIT == 1) {
+                v = hist[idx];
+            } else {
+                v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
+                hist[hw + idx] = 0;
+            }
+            hist[idx] = 0;
+            if (p < d && v != 0) atomicAdd(orow + b, (unsigned long long)v);
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
         const int b = idx / Dt, col = idx - b * Dt;
         const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
