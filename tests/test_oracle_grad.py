@@ -111,3 +111,32 @@ def test_cubical_and_simplicial_adjoints_agree_on_a_path(oracle):
     a = oracle.wect_backward_cubical([L], vw, dirs, 8, -1.0, 1.0, G, 0.5)
     b = oracle.wect_backward_simplicial(X, vw, [E], dirs, 8, -1.0, 1.0, G, 0.5)
     assert np.array_equal(a, b)
+
+
+# Tie-break of the adjoint, worked by hand from its definition.  The path of 4 vertices at
+# x = -1, -1/3, 1/3, 1 (a 1-D grid of length 4), weights w = (5, 9, 9, 2), direction s = (1),
+# T = 3 over [-1, 1]: beta = (-1, 0, 1), and bin(h) = #{q <= 1 : beta[q] < h} gives the vertex
+# bins (0, 1, 2, 2).  A cell's bin is that of its highest vertex: edges (0,1) -> 1, (1,2) -> 2,
+# (2,3) -> 2.  Upstream G = (1, 10, 100), suffix sums S = (111, 110, 100).
+#   vertices (sign +): I0 += S[0] = 111, I1 += S[1] = 110, I2 += S[2] = 100, I3 += S[2] = 100
+#   edge (0,1), heaviest vertex 1:                 I1 -= S[1] -> I1 = 0
+#   edge (1,2), weights 9 = 9, lowest index is 1:  I1 -= S[2] -> I1 = -100
+#   edge (2,3), heaviest vertex 2:                 I2 -= S[2] -> I2 = 0
+# so I = (111, -100, 0, 100).  Routing the tie to the highest index would give (111, 0, -100, 100).
+_TIE_W = np.array([5, 9, 9, 2], dtype=np.int64)
+_TIE_G = np.array([[1, 10, 100]], dtype=np.int64)
+_TIE_I = np.array([111, -100, 0, 100], dtype=np.float32)
+
+
+def test_adjoint_tie_break_cubical_by_hand(oracle):
+    g = oracle.wect_backward_cubical([4], _TIE_W, np.array([[1.0]]), 3, -1.0, 1.0, _TIE_G, 1.0)
+    assert np.array_equal(g, _TIE_I)
+
+
+def test_adjoint_tie_break_simplicial_by_hand(oracle):
+    """The same path as a simplicial complex, with the tied edge listed as (2, 1): the tie goes
+    to the lower vertex index, not to the first vertex of the row."""
+    X = np.array([[-1.0], [-1.0 / 3.0], [1.0 / 3.0], [1.0]])
+    E = np.array([[0, 1], [2, 1], [2, 3]], dtype=np.int32)
+    g = oracle.wect_backward_simplicial(X, _TIE_W, [E], np.array([[1.0]]), 3, -1.0, 1.0, _TIE_G, 1.0)
+    assert np.array_equal(g, _TIE_I)

@@ -450,3 +450,50 @@ def test_default_range_is_max_abs_height(oracle):
     lo, hi = oracle.default_range_simplicial(cx.coords, dirs)
     M = max(abs(sum(Fraction(cx.coords[v, a]) * Fraction(dirs[p, a]) for a in range(2))) for v in range(cx.nv) for p in range(3))
     assert hi == float(M) and lo == -hi
+
+
+def _grid_axis_coords(L):
+    """Exact rational grid coordinates (2i - (L-1)) / (L-1) of one axis (0 when L = 1)."""
+    return [Fraction(0) if L == 1 else Fraction(2 * i - (L - 1), L - 1) for i in range(L)]
+
+
+@pytest.mark.parametrize("dims", [[9], [5, 17], [9, 3, 5]])
+def test_grid_default_range_exact_dyadic(oracle, dims):
+    """Default range [-M, M] of a grid (Section 3, the definition of M) against the exact rational
+    max of |x(v) . s| over every vertex and direction.  L - 1 is a power of two and the direction
+    components are dyadic, so every height is exact.  The data put the largest |h| in the last
+    direction, with the last axis contributing: a skipped axis or a direction left out would each
+    change M (the grid is symmetric about 0, so max h = -min h)."""
+    n = len(dims)
+    base = [[0.5, -0.25, 0.125], [-0.25, 0.5, 0.25], [-0.75, -0.5, -1.0]]
+    if n == 1:
+        base = [[0.5], [0.25], [-0.75]]
+    dirs = np.array([row[:n] for row in base], dtype=np.float64)
+    axes = [_grid_axis_coords(L) for L in dims]
+    M = Fraction(0)
+    for idx in itertools.product(*[range(L) for L in dims]):
+        for s in dirs:
+            M = max(M, abs(sum(axes[a][idx[a]] * Fraction(s[a]) for a in range(n))))
+    lo, hi = oracle.default_range_grid(dims, dirs)
+    assert hi == float(M) and lo == -hi
+    # the same M once the last direction or the last axis is dropped is smaller
+    assert oracle.default_range_grid(dims, dirs[:2])[1] < hi
+    if n > 1:
+        assert oracle.default_range_grid(dims[:-1], np.ascontiguousarray(dirs[:, :-1]))[1] < hi
+
+
+@pytest.mark.parametrize("dims", [[7], [6, 11], [7, 6, 11]])
+def test_grid_default_range_with_rounding(oracle, dims):
+    """Non-dyadic grid coordinates and Fibonacci directions: M equals the max of |h| over every
+    vertex, with h from the independent restatement of the height rounding rule (exact rational
+    coordinates rounded once, then the fma chain)."""
+    n = len(dims)
+    dirs = S.fibonacci_directions(9)[:, :n] if n == 3 else S.random_directions(9, n, seed=41)
+    axes = [[rn(c) for c in _grid_axis_coords(L)] for L in dims]
+    M = 0.0
+    for idx in itertools.product(*[range(L) for L in dims]):
+        x = [axes[a][idx[a]] for a in range(n)]
+        for s in dirs:
+            M = max(M, abs(height_reading(x, list(s))))
+    lo, hi = oracle.default_range_grid(dims, np.ascontiguousarray(dirs))
+    assert hi == M and lo == -M
