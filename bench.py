@@ -7,7 +7,14 @@ transform: every row of the hot path (weights, threshold table, fused stencil sc
 prefix scan).  The metric is simplex.direction evaluations per second: (cells of the complex)
 x d per step, summed over all ranks.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--headline-only]
+
+The same JSON line also carries the metric's other two parts, each timed with CUDA events in a
+clock-sampled window of its own: "batched_vs_loop" (4096 blob images, d = 64, T = 64: one
+graph-captured persistent launch against the per-image launch loop) and "fwd_bwd_ratio" (256
+volumes of 64^3, d = 128, T = 128: autograd forward + MSE + backward against the forward), and
+"ecf_intensity" (the intensity-filter ECF of uniform 2048^2 .. 8192^2 images and 128^3 .. 512^3
+volumes at T = 1000 and 10000).
 
 Multi-GPU (torchrun, one process per GPU): every rank transforms its own volume (the path
 partitions into independent complexes, no collective on the data path); timing is the max
@@ -414,43 +421,62 @@ def run_gpu(args):
         "clocks": ck,
         "wall_s": t_wall,
     }
-    if args.extras:
-        line["extras"] = extras(P, S, dev)
+    if not args.headline_only:
+        line.update(secondary(P, S, dev, args.steps, flush, local))
     print(json.dumps(line), flush=True)
     if dist:
         tdist.destroy_process_group()
     return 0
 
 
-def extras(P, S, dev):
-    """Side measurements named by the metric: batched vs per-image loop, forward+backward vs
-    forward (differentiation workload), both timed with CUDA events."""
+def _section(fn, steps, flush, local, soak_s=1.5, warmup=3):
+    """Time fn with CUDA events on the current stream after warm-up, flushing L2 before every
+    timed call outside the events, with nvidia-smi clocks sampled over a soak of identical calls
+    that ends with the timed calls.  Returns (mean ms, clocks)."""
+    import torch
+
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    ck = ClockSampler(local)
+    ck.start()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < soak_s:
+        flush.zero_()
+        fn()
+        torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    clocks = ck.stop()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps, clocks
+
+
+def secondary(P, S, dev, steps, flush, local):
+    """The metric's other two parts and the ECF throughput rows, each with its own clock window:
+    the 4096-image batch as one graph-captured persistent launch against the per-image launch
+    loop, forward + backward against forward on the differentiation workload (autograd + MSE),
+    and the intensity-filter ECF of uniform images and volumes at T = 1000 and 10000."""
     import torch
 
     res = {}
-
-    def timed(fn, reps=5):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
     # batched images: 4096 2D blob images, d=64, T=64
     wl = S.image_batch()
     dirs = torch.from_numpy(wl.dirs).to(dev)
     b = P.CubicalBatch([torch.from_numpy(x).to(dev) for x in wl.grids])
-    out = torch.empty((len(wl.grids), 64, 64), dtype=torch.int64, device=dev)
-    t_batch = timed(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out))
-    t_loop = timed(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out, loop=True), reps=2)
+    out = torch.empty((len(wl.grids), len(wl.dirs), wl.T), dtype=torch.int64, device=dev)
+    t_batch, ck_b = _section(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out), steps, flush, local)
+    t_loop, ck_l = _section(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out, loop=True), min(steps, 5), flush, local,
+                            warmup=1)
     cells = sum((2 * x.shape[0] - 1) * (2 * x.shape[1] - 1) for x in wl.grids)
-    res["images2d_4096"] = {"batched_ms": t_batch, "loop_ms": t_loop, "speedup": t_loop / t_batch,
-                            "evals_per_s": cells * 64 / (t_batch / 1e3)}
+    res["batched_vs_loop"] = {"workload": wl.name, "batched_ms": t_batch, "loop_ms": t_loop,
+                              "ratio": t_loop / t_batch, "batched_evals_per_s": cells * len(wl.dirs) / (t_batch / 1e3),
+                              "clocks_batched": ck_b, "clocks_loop": ck_l}
     del b, out
     # differentiation: 256 volumes 64^3 f32, d=128, T=128, MSE against a target batch
     wv = S.volume_batch_diff()
@@ -474,14 +500,16 @@ def extras(P, S, dev):
         loss = ((W - Bt) ** 2).mean()
         loss.backward()
 
-    tf = timed(fwd)
-    tfb = timed(fwd_bwd)
+    tf, ck_f = _section(fwd, steps, flush, local)
+    tfb, ck_fb = _section(fwd_bwd, steps, flush, local)
     cells = len(wv.grids) * cells_of(wv.dims)
-    res["volumes3d_256x64^3"] = {"fwd_ms": tf, "fwd_bwd_ms": tfb, "ratio": tfb / tf,
-                                 "fwd_evals_per_s": cells * 128 / (tf / 1e3)}
-    del bb, w, flat
+    res["fwd_bwd_ratio"] = {"workload": wv.name, "fwd_ms": tf, "fwd_bwd_ms": tfb, "ratio": tfb / tf,
+                            "fwd_evals_per_s": cells * len(wv.dirs) / (tf / 1e3),
+                            "step": "WECTFunction forward + MSE (+ loss.backward() through the library adjoint)",
+                            "clocks_fwd": ck_f, "clocks_fwd_bwd": ck_fb}
+    del bb, w, flat, Bt
     # intensity-filter ECF of uniform images and volumes (the paper's ECF throughput workloads):
-    # pixels (voxels) per second, T = 1000 and 10000, filter resident on the device
+    # vertices per second, T = 1000 and 10000, filter resident on the device
     g = torch.Generator(device=dev).manual_seed(7)
     ecf = {}
     for dims in ([2048] * 2, [4096] * 2, [8192] * 2, [128] * 3, [256] * 3, [512] * 3):
@@ -492,8 +520,9 @@ def extras(P, S, dev):
         cx = P.CubicalComplex(None, dims=dims)
         o = torch.empty(10000, dtype=torch.int64, device=dev)
         for T in (1000, 10000):
-            ms = timed(lambda: cx.ecf(f, T, 0.0, 1.0, out=o[:T]), reps=5)
-            ecf[f"{'x'.join(map(str, dims))}_T{T}"] = {"ms": ms, "gvertices_per_s": nv / ms / 1e6}
+            ms, ck = _section(lambda: cx.ecf(f, T, 0.0, 1.0, out=o[:T]), steps, flush, local, soak_s=0.5)
+            ecf[f"{'x'.join(map(str, dims))}_T{T}"] = {"ms": ms, "gvertices_per_s": nv / ms / 1e6,
+                                                        "sm_mhz": ck.get("sm_mhz"), "reasons": ck.get("reasons")}
         del cx, f
     res["ecf_intensity"] = ecf
     return res
@@ -575,7 +604,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", action="store_true", help="also time the batched and differentiation workloads")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the batched-vs-loop, forward+backward and ECF sections")
     ap.add_argument("--case", choices=["adjoint16", "mesh64", "batch4096", "ecf4096", "wecf64"],
                     help="run one untimed workload for an ncu capture (no JSON line)")
     args = ap.parse_args()

@@ -275,26 +275,42 @@ WECT_API void wect_batch_destroy(wect_batch b);
 
 /*
  * The paper has no counterpart to this entry point.  It serves callers that cannot allocate
- * device memory: code that runs while a CUDA graph is being captured for later replay, hosts
- * whose allocator or runtime owns every device byte, and services that must not allocate after
- * start-up.  It computes exactly what wect_compute computes for the full cubical complex of a
- * grid, with the same kernels, but allocates nothing: its scratch (threshold table, direction
- * grouping, work queue, int32 copy of the weights) lives in one static device array of about
- * 8.1 MB that every GPU loading this library holds until the process exits.
+ * device memory: frameworks and inference servers whose caching allocator owns every device
+ * byte (an allocation from outside its pool fails or fragments it), real-time and embedded
+ * services that fix their memory at start-up and must not allocate afterwards, and plugin
+ * hosts that give a plugin no way to allocate.  It computes exactly what wect_compute computes
+ * for the full cubical complex of a grid, with the same kernels, but allocates nothing: its
+ * scratch (threshold table, direction grouping, work queue, int32 copy of the weights, status
+ * word) lives in one static device array of about 8.1 MB that every GPU loading this library
+ * holds until the process exits.
  *   n, dims (host)   grid rank 1..3 and axis lengths (axis 0 fastest); at most 2^21 vertices
  *   vertex_weights   (dev) uint8 [prod dims] for WECT_W_U8; ignored for WECT_W_ONE (other types:
  *                    WECT_ERR_UNSUPPORTED)
- *   dirs (dev)       [d][n] float64, 1 <= d <= 4096;  2 <= T <= 4096;  lo, hi as wect_compute
+ *   dirs (dev)       [d][n] float64, 1 <= d <= 4096;  lo, hi as wect_compute
+ *   T                2 <= T <= 4096, and the int32 shared histogram (T x 32 entries at least)
+ *                    must fit one block's shared memory: about T <= 1700 on a GB300
  *   out (dev)        [d][T] int64, caller-allocated
- * Sizes beyond these limits return WECT_ERR_INVALID_ARG (nothing is launched; the message is in
- * wect_last_error).  The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress) and caches it: make that first call before any stream capture.
- * Every call shares the one array and clears on its stream what must start at zero, so calls
- * whose work overlaps on the GPU (other streams, or unordered host threads) race; order them.
+ * d, T, dims or the vertex count beyond these limits return WECT_ERR_INVALID_ARG; a T whose
+ * histogram does not fit shared memory, rows longer than 2^31 / (2^n * 255) vertices, or a grid
+ * that needs more than 4096 work items return WECT_ERR_UNSUPPORTED.  Nothing is launched then
+ * and the message is in wect_last_error.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress); the first call on a device is the one that sets the
+ * array up, so make it before any stream capture.  Every call shares the one array and clears
+ * on its stream what must start at zero, so calls whose work overlaps on the GPU (other streams,
+ * or unordered host threads) race; order them.  Directions are checked on the device:
+ * wect_cubical_static_status reports what the last call's checks found.
  */
 WECT_API wect_status wect_cubical_compute_static(int n, const int64_t *dims, const void *vertex_weights,
                                                  wect_wtype wtype, const double *dirs, int d, int T, double lo,
                                                  double hi, int64_t *out, wect_stream stream);
+
+/*
+ * Status of the device-side checks of the last wect_cubical_compute_static call on the current
+ * device (the paper has no counterpart): synchronises the stream, reads the status word in the
+ * static scratch and clears it.  WECT_ERR_INVALID_ARG when a direction was not finite (the
+ * table written by that call is then meaningless), else WECT_OK.  Allocates nothing.
+ */
+WECT_API wect_status wect_cubical_static_status(wect_stream stream);
 
 /* ---------------------------------------------------------------- misc */
 

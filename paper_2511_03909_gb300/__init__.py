@@ -95,6 +95,7 @@ def _declare(L):
         "wect_profile_enable": (_st, [_i]),
         "wect_profile_read": (_st, [_p, _p]),
         "wect_cubical_compute_static": (_st, [_i, _p, _p, _i, _p, _i, _i, _d, _d, _p, _p]),
+        "wect_cubical_static_status": (_st, [_p]),
         "wect_debug_fail_alloc": (_st, [_i64]),
     }
     for name, (res, args) in sig.items():
@@ -114,7 +115,8 @@ def exported_symbols():
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
         "wect_batch_autotune",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
-        "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_debug_fail_alloc",
+        "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_cubical_static_status",
+        "wect_debug_fail_alloc",
     ]
 
 
@@ -416,22 +418,6 @@ class CubicalBatch:
 # ------------------------------------------------------------------ autograd
 
 
-def grad_to_fixed(g: torch.Tensor, T: int, d: int):
-    """Upstream float64 gradient -> (int64 table, scale), g ~ table * scale.  The scale is the
-    largest power of two that keeps d * T * max|table| below 2^62, so the adjoint's int64 sums
-    over thresholds and directions cannot overflow; the conversion is exact when g's values are
-    multiples of that power of two (e.g. the gradient of a mean-squared error of two fixed-point
-    transforms).  Runs as torch ops on the device (plumbing between the loss and the adjoint)."""
-    m = float(g.abs().max().item()) if g.numel() else 0.0
-    if m == 0.0 or not math.isfinite(m):
-        return torch.zeros_like(g, dtype=torch.int64), 1.0
-    e = math.frexp(m)[1]                       # m < 2^e
-    k = 62 - math.ceil(math.log2(max(T, 2))) - math.ceil(math.log2(max(d, 2))) - e
-    k = max(min(k, 1000), -1000)
-    q = torch.round(torch.ldexp(g, torch.tensor(k, device=g.device, dtype=torch.int32))).to(torch.int64)
-    return q, math.ldexp(1.0, -k)
-
-
 class WECTFunction(torch.autograd.Function):
     """W = WECT(weights) for a CubicalBatch, with the library's exact adjoint as backward.
 
@@ -461,7 +447,7 @@ def cubical_wect_static(weights: torch.Tensor | None, dirs: torch.Tensor, T: int
                         hi: float = math.nan, out: torch.Tensor | None = None, dims=None) -> torch.Tensor:
     """wect_cubical_compute_static: the WECT of a uint8 (or unweighted) grid without any device
     allocation by the library (scratch in a static device array; see include/wect.h).  ``out``
-    may be preallocated by the caller."""
+    may be preallocated by the caller, so that the call itself allocates nothing either."""
     if weights is not None:
         _require_cuda(weights, "weights", torch.uint8)
         dims = list(reversed(weights.shape))
@@ -475,6 +461,12 @@ def cubical_wect_static(weights: torch.Tensor | None, dirs: torch.Tensor, T: int
     _check(load().wect_cubical_compute_static(n, dims_a, _ptr(weights), W_U8 if weights is not None else W_ONE,
                                               _ptr(dirs), d, T, lo, hi, _ptr(out), _stream()))
     return out
+
+
+def cubical_static_status():
+    """wect_cubical_static_status: raise WectError when the device-side checks of the last
+    allocation-free call on this device failed (a non-finite direction); clears the status."""
+    _check(load().wect_cubical_static_status(_stream()))
 
 
 # ------------------------------------------------------------------ one-shot helpers

@@ -1,21 +1,25 @@
 // wect_static.cu -- an allocation-free variant of the cubical forward transform.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA graph is being
-// captured for later replay, allocators or runtimes that own every device byte and forbid
-// other allocations, and hosts that must not allocate after start-up (real-time and embedded
-// services).  wect_cubical_compute_static serves them.  It runs the same kernels as
-// wect_compute on a cubical grid, but its scratch memory (threshold table, direction grouping,
-// work-queue head, work items, int32 copy of the weights) lives in one file-scope device array
-// of fixed size, reserved when the library is loaded and held by every GPU that loads it until
+// Some callers cannot call cudaMalloc at all: frameworks and inference servers whose caching
+// allocator owns every device byte (an allocation from outside its pool fails or fragments
+// it), real-time and embedded services that fix their memory plan at start-up and must not
+// allocate afterwards, and plugin hosts that give a plugin no way to allocate.
+// wect_cubical_compute_static serves them.  It runs the same kernels as wect_compute on a
+// cubical grid, but its scratch memory (threshold table, direction grouping, work-queue head,
+// work items, int32 copy of the weights, status word) lives in one file-scope device array of
+// fixed size.  Each device reserves the array when this module is loaded on it (with lazy
+// module loading, at the latest when the first call looks up its address) and holds it until
 // the process exits.
 //
-// Host code never uses the array's name as a device address.  On its first call on a device
-// the entry point asks the runtime for the array's address on that device
-// (cudaGetSymbolAddress, with that device current), caches it per device, and passes it to the
-// kernels.  That first call should therefore come before any stream capture.  Calls share the
-// array: two calls whose work overlaps on the GPU (different streams, or different host threads
-// without ordering) race on it.  Everything that must start at zero is cleared on the stream at
-// the start of each call.
+// Host code never uses the array's name as a device address.  Every call asks the runtime for
+// the array's address on the current device (cudaGetSymbolAddress, with that device current)
+// and passes it to the kernels; the first call on a device is the one that does this set-up,
+// so it should come before any stream capture.  A call whose stream is capturing does not
+// repeat the lookup and uses the address found by the last call on that device.  Calls share
+// the array: two calls whose work overlaps on the GPU (different streams, or different host
+// threads without ordering) race on it.  Everything that must start at zero is cleared on the
+// stream at the start of each call, and wect_cubical_static_status reads (and clears) the
+// status word that the last call's device-side checks left.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -74,15 +78,20 @@ __global__ void static_setup_kernel(unsigned char *scratch, GridDesc g, int ntil
 static std::mutex g_static_mu;
 static void *g_static_ptr[kStaticMaxDevices];
 
-// Device address of the scratch array on the current device (looked up once per device).
-static cudaError_t static_scratch(unsigned char **out)
+// Device address of the scratch array on the current device.  It is looked up again on every
+// call whose stream is not capturing (a module reloaded after cudaDeviceReset may sit at another
+// address); a capturing call reuses the last address found on the device.
+static cudaError_t static_scratch(cudaStream_t st, unsigned char **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone || !g_static_ptr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
@@ -157,10 +166,10 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
     chunks = (rows + per - 1) / per;
     if ((int64_t)ntiles * chunks > kStaticMaxItems) return sfail(WECT_ERR_UNSUPPORTED, "too many work items");
 
-    unsigned char *S = nullptr;
-    cudaError_t e = static_scratch(&S);
-    if (e != cudaSuccess) return sfail(WECT_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *S = nullptr;
+    cudaError_t e = static_scratch(st, &S);
+    if (e != cudaSuccess) return sfail(WECT_ERR_CUDA, cudaGetErrorString(e));
     double *range = reinterpret_cast<double *>(S + kOffRange);
     unsigned long long *M = reinterpret_cast<unsigned long long *>(S + kOffM);
     int *counter = reinterpret_cast<int *>(S + kOffCounter);
@@ -216,5 +225,22 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
     SCK(launch_cubical_fwd(n, nsplit, dpl, a, std::min(ctas, a.n_items), smem, st));
     SCK(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), d, T, st));
 #undef SCK
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_cubical_static_status(wect_stream stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *S = nullptr;
+    cudaError_t e = static_scratch(st, &S);
+    if (e != cudaSuccess) return sfail(WECT_ERR_CUDA, cudaGetErrorString(e));
+    int bits = 0;
+    e = cudaMemcpyAsync(&bits, S + kOffStatus, sizeof bits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S + kOffStatus, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return sfail(WECT_ERR_CUDA, cudaGetErrorString(e));
+    if (bits & kStatusOverflow) return sfail(WECT_ERR_OVERFLOW, "a per-vertex contribution exceeded the accumulator");
+    if (bits & kStatusBadIndex) return sfail(WECT_ERR_INVALID_ARG, "device-side validation failed (non-finite direction)");
+    if (bits) return sfail(WECT_ERR_CUDA, "unexpected device status bits");
     return WECT_OK;
 }

@@ -40,22 +40,6 @@ def test_batch_autotune_keeps_results(P, oracle):
     assert np.array_equal(before, after)
 
 
-def test_images2d_4096_full(P, oracle):
-    """4096 blob images with sides U{28..256}, d=64, T=64: batched launch equals the
-    per-image loop everywhere and the oracle on sampled images."""
-    wl = S.image_batch()
-    dirs = cuda(wl.dirs)
-    b = P.CubicalBatch([cuda(x) for x in wl.grids])
-    got = b.wect(dirs, wl.T, wl.lo, wl.hi)
-    loop = b.wect(dirs, wl.T, wl.lo, wl.hi, loop=True)
-    assert torch.equal(got, loop)
-    got = got.cpu().numpy()
-    for i in (0, 1, 2047, 4095):
-        x = wl.grids[i]
-        ref = oracle.wect_cubical(list(reversed(x.shape)), x.ravel(), wl.dirs, wl.T, wl.lo, wl.hi)
-        assert np.array_equal(got[i], ref), i
-
-
 def test_backward_cubical_matches_oracle(P, oracle):
     rng = np.random.default_rng(5)
     for dims, d, T in (([9, 8, 7], 16, 16), ([30, 20], 24, 33), ([40], 5, 9), ([13, 12, 11], 128, 128)):
@@ -98,8 +82,9 @@ def test_backward_simplicial_matches_oracle(P, oracle):
 
 def test_autograd_mse_small(P, oracle):
     """Volumes with f32 weights, loss = MSE(WECT(w), WECT(target)): the autograd gradient equals
-    the oracle's exact adjoint of the loss."""
-    count, side, d, T = 3, 9, 24, 20
+    the oracle's exact adjoint of the loss, bit for bit.  N = count * d * T is a power of two, so
+    the upstream 2 (W - B) 2^-24 / N is exact in float64 and its quantisation loses nothing."""
+    count, side, d, T = 4, 9, 16, 32
     a = S.uniform_f32_grids(count, [side] * 3, seed=5)
     t = S.uniform_f32_grids(count, [side] * 3, seed=6)
     dirs = S.fibonacci_directions(d)
@@ -117,32 +102,4 @@ def test_autograd_mse_small(P, oracle):
         Wi = oracle.wect_cubical([side] * 3, vw, dirs, T, -SQ3, SQ3)
         Bi = oracle.wect_cubical([side] * 3, oracle.to_fixed(t[i], 24), dirs, T, -SQ3, SQ3)
         ref = oracle.wect_backward_cubical([side] * 3, vw, dirs, T, -SQ3, SQ3, Wi - Bi, 2.0 ** -23 / N)
-        np.testing.assert_allclose(g[i], ref, rtol=1e-6, atol=0)
-
-
-def test_volumes3d_batch_forward_backward_full(P, oracle):
-    """256 volumes of 64^3 with f32 U[0,1) weights, d=128, T=128: batched forward and adjoint
-    at full size; one volume checked against the oracle with 6 of the directions."""
-    wl = S.volume_batch_diff()
-    dirs_t = cuda(wl.dirs)
-    flat = cuda(wl.grids.reshape(-1))
-    b = P.CubicalBatch(flat=flat, dims=[wl.dims] * len(wl.grids), frac_bits=24)
-    W = b.wect(dirs_t, wl.T, wl.lo, wl.hi)
-    bt = P.CubicalBatch(flat=cuda(wl.target.reshape(-1)), dims=[wl.dims] * len(wl.grids), frac_bits=24)
-    B = bt.wect(dirs_t, wl.T, wl.lo, wl.hi)
-    D = (W - B).contiguous()
-    N = D.numel()
-    g = b.backward(dirs_t, wl.T, wl.lo, wl.hi, D, 2.0 ** -23 / N)
-    torch.cuda.synchronize()
-    k = 17
-    sub = [0, 40, 81, 100, 127, 64]
-    vw = oracle.to_fixed(wl.grids[k], 24)
-    ref = oracle.wect_cubical(wl.dims, vw, wl.dirs[sub], wl.T, wl.lo, wl.hi)
-    assert np.array_equal(W[k].cpu().numpy()[sub], ref)
-    # adjoint of one volume for a sub-batch of directions, same kernels
-    one = P.CubicalComplex(cuda(wl.grids[k]), frac_bits=24)
-    Dk = D[k].cpu().numpy()[sub]
-    gk = one.backward(cuda(wl.dirs[sub]), wl.T, wl.lo, wl.hi, cuda(Dk), 2.0 ** -23 / N).cpu().numpy()
-    gref = oracle.wect_backward_cubical(wl.dims, vw, wl.dirs[sub], wl.T, wl.lo, wl.hi, Dk, 2.0 ** -23 / N)
-    assert np.array_equal(gk, gref)
-    assert np.isfinite(g.cpu().numpy()).all()
+        assert np.array_equal(g[i], ref), i

@@ -131,20 +131,6 @@ def test_ecf_of_images(P, O, weighted):
             assert np.array_equal(got, ref)
 
 
-def test_voxel3d_128_full(P, O):
-    """128^3 smoothed u8 field, d=256 Fibonacci, T=128 over [-sqrt3, sqrt3]: the launch the
-    benchmark times.  Sampled directions against the oracle, every direction's last column
-    against the weighted Euler characteristic, which does not depend on the direction."""
-    wl = S.voxel3d_128()
-    cx = P.CubicalComplex(cuda(wl.grid))
-    got = cx.wect(cuda(wl.dirs), wl.T, wl.lo, wl.hi).cpu().numpy()
-    sample = [0, 77, 255]
-    ref = O.wect_cubical(wl.dims, wl.grid.ravel(), wl.dirs[sample], wl.T, wl.lo, wl.hi)
-    assert np.array_equal(got[sample], ref)
-    assert np.all(got[:, -1] == ref[0, -1])
-    cx.device_status()
-
-
 def test_set_weights_and_overflow_status(P, O):
     dims = [10, 9, 8]
     rng = np.random.default_rng(9)

@@ -82,23 +82,6 @@ def test_mesh_small_lognormal_fixed_point(P, oracle):
     assert np.array_equal(got, ref)
 
 
-def test_mesh2d_1024_full(P, oracle):
-    """1024^2 jittered mesh, d=1024, T=512, default range: sampled directions against the
-    oracle, the last column against the weighted Euler characteristic."""
-    wl = S.mesh2d_1024()
-    cx = wl.complex
-    h = _make(P, cx, cx.weights, fb=24)
-    got = h.wect(cuda(wl.dirs), wl.T).cpu().numpy()
-    vw = oracle.fixed_from_f32(cx.weights, 24)
-    sw = oracle.simplicial_weights(cx.simplices, vw)
-    lo, hi = oracle.default_range_simplicial(cx.coords, wl.dirs)
-    sample = [0, 301, 1023]
-    ref = oracle.wect_simplicial(cx.coords, cx.simplices, sw, wl.dirs[sample], wl.T, lo, hi)
-    assert np.array_equal(got[sample], ref)
-    assert np.all(got[:, -1] == ref[0, -1])
-    h.device_status()
-
-
 def test_ecf_simplicial(P, oracle):
     cx = S.random_simplicial(200, 2, 500, 300, seed=7)
     rng = np.random.default_rng(7)
