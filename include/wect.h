@@ -161,6 +161,11 @@ WECT_API void wect_complex_destroy(wect_complex cx);
  *               M = max over directions and vertices of |h_p(v)| (computed exactly on the
  *               device); otherwise lo <= hi, finite.
  *   out (dev)   [d][T] int64, row p = WECF of direction p at thresholds beta[0..T-1]
+ * Errors: INVALID_ARG for NULL pointers, d < 1, T < 2 or a bad range; UNSUPPORTED for
+ * T > 65535, or on a cubical grid whose axis-0 rows are longer than the stencil kernel's shared
+ * row buffers hold (about 800 vertices for n = 3, 1,600 for n = 2, 3,200 for n = 1).  Every
+ * T up to 65535 is supported: when the int32 histograms of a direction tile do not fit shared
+ * memory, the kernels add each update to the int64 table in global memory instead.
  */
 WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
                          int64_t *out, wect_stream stream);
@@ -208,6 +213,9 @@ WECT_API wect_status wecf_compute(wect_complex cx, const double *filters, int m,
  * (cubical, or simplicial in MAX_OF_VERTICES mode) are supported.
  *   dW (dev)      [d][T] int64 upstream gradient in fixed-point units
  *   grad_w (dev)  [k_0] float32
+ * Errors: as wect_compute; on a cubical grid the octant sums stage the suffix rows of a chunk of
+ * directions in shared memory (chunks shrink as d x T grows), and T beyond one direction's
+ * row in shared memory (about T > 14,000) returns UNSUPPORTED.
  */
 WECT_API wect_status wect_backward(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
                           const int64_t *dW, double scale, float *grad_w, wect_stream stream);
@@ -286,13 +294,12 @@ WECT_API void wect_batch_destroy(wect_batch b);
  *   n, dims (host)   grid rank 1..3 and axis lengths (axis 0 fastest); at most 2^21 vertices
  *   vertex_weights   (dev) uint8 [prod dims] for WECT_W_U8; ignored for WECT_W_ONE (other types:
  *                    WECT_ERR_UNSUPPORTED)
- *   dirs (dev)       [d][n] float64, 1 <= d <= 4096;  lo, hi as wect_compute
- *   T                2 <= T <= 4096, and the int32 shared histogram (T x 32 entries at least)
- *                    must fit one block's shared memory: about T <= 1700 on a GB300
+ *   dirs (dev)       [d][n] float64, 1 <= d <= 4096;  2 <= T <= 4096;  lo, hi as wect_compute
  *   out (dev)        [d][T] int64, caller-allocated
- * d, T, dims or the vertex count beyond these limits return WECT_ERR_INVALID_ARG; a T whose
- * histogram does not fit shared memory, rows longer than 2^31 / (2^n * 255) vertices, or a grid
- * that needs more than 4096 work items return WECT_ERR_UNSUPPORTED.  Nothing is launched then
+ * d, T, dims or the vertex count beyond these limits return WECT_ERR_INVALID_ARG; rows (axis 0)
+ * longer than the kernel's shared row buffers hold (about 800 vertices for n = 3, 1,600 for
+ * n = 2, 3,200 for n = 1) or a grid that needs more than 4096 work items return
+ * WECT_ERR_UNSUPPORTED.  Nothing is launched then
  * and the message is in wect_last_error.  Every call looks up the array's device address on the
  * current device (cudaGetSymbolAddress); the first call on a device is the one that sets the
  * array up, so make it before any stream capture.  Every call shares the one array and clears

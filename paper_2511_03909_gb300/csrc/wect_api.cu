@@ -337,6 +337,7 @@ static wect_status choose_cubical_mode(int n, int wt, uint64_t wmax, int &nsplit
 struct CubShape {
     int dpl, Dt, ctas_per_sm, grid;
     size_t smem;
+    bool gh = false;              // global-histogram variant (T x Dt does not fit shared memory)
 };
 
 // Tile shape of the stencil kernel: the widest direction tile (fewest passes over the grid)
@@ -365,11 +366,24 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
             k = std::max(1, std::min(k, 2048 / threads));
             out.ctas_per_sm = k;
             out.grid = sm_count() * k;
+            out.gh = false;
             return true;
         }
         if (Dt_req > 0) break;
     }
-    return false;
+    if (dpl_req > 0 || Dt_req > 0) return false;
+    // no shared histogram fits: scatter into the global int64 difference table instead
+    const int Dt = std::min(Dmax, 256);
+    out.dpl = Dt >= 64 ? 2 : 1;
+    out.Dt = Dt;
+    out.smem = cubical_fwd_smem(n, 1, out.dpl, T, Dt, maxL0, true);
+    if (out.smem > limit) return false;
+    int k = (int)(smem_per_sm() / (out.smem + 2048));
+    k = std::max(1, std::min(k, 2048 / threads));
+    out.ctas_per_sm = k;
+    out.grid = sm_count() * k;
+    out.gh = true;
+    return true;
 }
 
 // Items for a set of grids: per complex, direction tiles x row chunks, largest first.  An item
@@ -457,9 +471,9 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
         cudaStreamIsCapturing(st, &cs);
         if (cs == cudaStreamCaptureStatusNone) {
             ProfScope prof(st);
-            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, a, grid, sh.smem, st), "cubical_fwd");
+            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st), "cubical_fwd");
         } else {
-            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, a, grid, sh.smem, st), "cubical_fwd");
+            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st), "cubical_fwd");
         }
     }
     if (!direct) KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), out_rows, T, st), "scan_rows");
@@ -845,13 +859,13 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
 {
     CubShape sh;
     if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh))
-        return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
-    if (c->L[0] > c->kflush) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
+        return fail(WECT_ERR_UNSUPPORTED, "grid rows of %d vertices do not fit the kernel's shared row buffers", c->L[0]);
+    if (c->L[0] > c->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
     wect_status s = ensure_common_ws(c->ws, T, d);
     if (s) return s;
     const int rows = c->L[1] * c->L[2];
     const bool direct = false;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, sh.grid);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), sh.grid);
     if (c->ws.items_key != key) {
         std::vector<GridDesc> gv(1);
         gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
@@ -886,8 +900,9 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
 {
     const int Dt = 32;
     const size_t sm = simplex_fwd_smem(c->nsplit, T, Dt);
-    if (sm > std::min<size_t>(smem_optin(), 200 * 1024))
-        return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
+    // T x 32 int32 entries beyond shared memory: every signed weight goes to the int64 table in
+    // global memory instead (same bins and sums)
+    const bool gh = sm > std::min<size_t>(smem_optin(), 200 * 1024);
     wect_status s = ensure_common_ws(c->ws, T);
     if (s) return s;
     CK(c->ws.bins.ensure((size_t)c->nv * Dt), "alloc bins");
@@ -914,6 +929,16 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
             // a multiple of 8 simplices, so that groups start on 16-byte boundaries
             a.chunk = std::max<int64_t>(8, std::min<int64_t>(c->kflush, std::max<int64_t>(4096, (a.k + grid - 1) / grid)) & ~7ll);
             a.out = reinterpret_cast<unsigned long long *>(out);
+            if (gh) {
+                // vertex bins of the tile first, then every list (vertices included) from the table
+                if (i == 0)
+                    KL(launch_vertex_bins(c->n, c->d_coords, c->d_xf, c->nv, dirs, c->ws.dtab.p, d, dt, Dt, T,
+                                          c->ws.beta.p, c->ws.bins.p, st),
+                       "vertex_bins");
+                const int g = (int)std::min<int64_t>(grid, (a.k + a.chunk - 1) / a.chunk);
+                KL(launch_simplex_fwd(c->nsplit, true, a, std::max(g, 1), st), "simplex_fwd");
+                continue;
+            }
             if (i == 0) {
                 // vertex bins of the tile, fused with the vertices' own scatter (16 warps x 8
                 // vertices per CTA step)
@@ -935,7 +960,7 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
                 continue;
             }
             const int g = (int)std::min<int64_t>(grid, (a.k + a.chunk - 1) / a.chunk);
-            KL(launch_simplex_fwd(c->nsplit, a, std::max(g, 1), st), "simplex_fwd");
+            KL(launch_simplex_fwd(c->nsplit, false, a, std::max(g, 1), st), "simplex_fwd");
         }
     }
     KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), d, T, st), "scan_rows");
@@ -1027,11 +1052,17 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     CK(ws.Rv.ensure((size_t)total_nv * noct), "alloc Rv");
     CK(ws.perm.ensure((size_t)d), "alloc perm");
     CK(ws.octb.ensure(9), "alloc octb");
-    // rows per filter tile: as many as fit next to the shared suffix table (up to 32)
+    // directions per chunk of the octant sums: the chunk's suffix rows ([dc + 1][T] int64) must fit
+    // shared memory next to one row tile of filter constants; then rows per filter tile: as many
+    // as fit (up to 32)
+    const size_t lim = smem_optin() - 1024;
+    int dc = d;
+    while (dc > 1 && cubical_bwd_rsum_smem(n, dc, T, 1) > lim) dc = (dc + 1) / 2;
+    if (cubical_bwd_rsum_smem(n, dc, T, 1) > lim)
+        return fail(WECT_ERR_UNSUPPORTED, "T = %d: one direction's suffix row does not fit the adjoint's shared table", T);
     int R = 32;
-    while (R > 1 && cubical_bwd_rsum_smem(n, d, T, R) > smem_optin() - 1024) R /= 2;
-    const size_t sm = cubical_bwd_rsum_smem(n, d, T, R);
-    if (sm > smem_optin() - 1024) return fail(WECT_ERR_UNSUPPORTED, "d x T too large for the adjoint's shared table");
+    while (R > 1 && cubical_bwd_rsum_smem(n, dc, T, R) > lim) R /= 2;
+    const size_t sm = cubical_bwd_rsum_smem(n, dc, T, R);
     auto key = std::make_tuple(d, R);
     if (ws.items_bwd_key != key) {
         std::vector<WorkItem> items;
@@ -1058,13 +1089,11 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     // the routing kernel sums in int64: 3^n d max|S| must stay below 2^63
     const int64_t pow3 = n == 1 ? 3 : (n == 2 ? 9 : 27);
     KL(launch_suffix_rows(dW, ws.S.p, (int64_t)n_grids * d, T, INT64_MAX / ((int64_t)d * pow3), status, st), "suffix_rows");
-    KL(launch_octant_sort(n, dirs, d, ws.perm.p, ws.octb.p, st), "octant_sort");
     CubicalBwdArgs a{};
     a.grids = d_grids;
     a.n_grids = n_grids;
     a.items = ws.items_bwd.p;
-    a.dirs = dirs;
-    a.d = d;
+    a.d_all = d;
     a.T = T;
     a.range = ws.range.p;
     a.beta = ws.beta.p;
@@ -1085,8 +1114,16 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
         if (hg.nv != a.uniform_nv) a.uniform_nv = 0;
     {
         ProfScope prof(st);
-        KL(launch_cubical_bwd(n, a, ws.n_items_bwd, sm, st), "cubical_bwd");
-        g_launches++;   // rsum + route
+        for (int p0 = 0; p0 < d; p0 += dc) {
+            const int dn = std::min(dc, d - p0);
+            KL(launch_octant_sort(n, dirs + (int64_t)p0 * n, dn, ws.perm.p, ws.octb.p, st), "octant_sort");
+            a.dirs = dirs + (int64_t)p0 * n;
+            a.d = dn;
+            a.p0 = p0;
+            a.accumulate = p0 > 0 ? 1 : 0;
+            KL(launch_cubical_bwd_rsum(n, a, ws.n_items_bwd, sm, st), "cubical_bwd_rsum");
+        }
+        KL(launch_cubical_bwd_route(n, a, st), "cubical_bwd_route");
     }
     return WECT_OK;
 }
@@ -1308,8 +1345,8 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
     int64_t maxnv = 0;
     for (auto &g : b->h_grids) maxnv = std::max<int64_t>(maxnv, g.nv);
     const int ntiles = (d + sh.Dt - 1) / sh.Dt;
-    direct = maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, direct ? 1 : 0);
+    direct = !sh.gh && maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), direct ? 1 : 0);
     if (b->ws.items_key == key) return WECT_OK;
     std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, T, b->kflush, 4 * sh.grid, direct);
     wect_status s = upload_items(b->ws, items, st);
@@ -1337,11 +1374,12 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
-    if (!batch_shape(b, d, T, sh)) return fail(WECT_ERR_UNSUPPORTED, "T = %d too large for the shared-memory histogram", T);
+    if (!batch_shape(b, d, T, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape of the stencil kernel fits (T = %d)", T);
+    if (b->maxL0 > b->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     bool direct = false;
     if ((s = batch_items(b, d, T, sh, direct, st))) return s;
-    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.dpl);
+    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.dpl * (sh.gh ? -1 : 1));
     auto it = b->graphs.find(key);
     if (it != b->graphs.end() && it->second.deps != graph_deps(b->ws)) {
         CK(cudaStreamSynchronize(st), "sync");          // a replay of it may still be running
@@ -1352,7 +1390,7 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     }
     if (it == b->graphs.end()) {
         // capture the launch sequence once on a private stream, replay it on the caller's stream
-        CK(prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.smem), "prepare");
+        CK(prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, sh.smem), "prepare");
         CK(cudaStreamSynchronize(st), "sync");
         GraphEntry ge;
         const int64_t before = g_launches.load();
@@ -1390,12 +1428,12 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
-    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "T too large");
-    if (b->maxL0 > b->kflush) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
+    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+    if (b->maxL0 > b->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     // one item list per complex, concatenated; each complex launched on its own
     std::vector<int> &starts = b->loop_starts;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl, 7);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), 7);
     if (b->ws.items_key != key) {
         std::vector<WorkItem> all;
         starts.assign(b->count + 1, 0);
@@ -1432,7 +1470,8 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.climit = b->climit;
         a.direct = 0;
         a.out = reinterpret_cast<unsigned long long *>(out);
-        KL(launch_cubical_fwd(b->n, b->nsplit, sh.dpl, a, std::max(1, std::min(sh.grid, a.n_items)), sh.smem, st), "fwd");
+        KL(launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, std::max(1, std::min(sh.grid, a.n_items)), sh.smem, st),
+           "fwd");
         KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out) + (int64_t)i * d * T, d, T, st), "scan");
     }
     return WECT_OK;
@@ -1529,7 +1568,12 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s) return s;
-    if (bc.Dt == 0) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+    if (bc.Dt == 0) {
+        // no shared-histogram shape fits this T: compute keeps the global-histogram shape
+        CubShape sh;
+        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+        return WECT_OK;
+    }
     b->tuned[{d, T}] = bc;
     for (auto &kv : b->graphs) {
         cudaGraphExecDestroy(kv.second.exec);

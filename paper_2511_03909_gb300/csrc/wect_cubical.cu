@@ -17,7 +17,10 @@
 // order, per-CTA int32 histograms [T][Dt] in shared memory (a column per direction, so the 32
 // lanes of a red.shared hit 32 distinct banks).  Wide weights use two int32 planes (low 16
 // bits unsigned, high part signed) so that 65536 updates per entry cannot overflow.  Partial
-// histograms are flushed into the int64 output with global atomics (exact, order-free).
+// histograms are flushed into the int64 output with global atomics (exact, order-free).  When
+// T x Dt int32 entries no longer fit shared memory (large T), the GH variant scatters every
+// update straight into the int64 difference table in global memory instead (same bins, same
+// integer sums; slower, but any T).
 #include "wect_device.cuh"
 #include "wect_launch.h"
 
@@ -171,10 +174,10 @@ __device__ __forceinline__ void cubical_flush_direct(int32_t *hist, int T, int D
 
 // The float32 filter could not decide the bin of vertex (i0,i1,i2) in direction p: evaluate the
 // float64 height, find its exact bin and move the contribution if the tentative bin was wrong.
-template <int N, int NSPLIT>
+template <int N, int NSPLIT, bool GH>
 __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDesc &g, int p, int i0, int i1, int i2,
                                            int thi, int nr, int col, uint32_t histAddr, int Dt, uint32_t HOFF,
-                                           int cv, int hv)
+                                           int cv, int hv, unsigned long long *oc)
 {
     const int T = P.T;
     const int bt = clamp_bin(thi, nr, T);
@@ -182,6 +185,14 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
                                 P.dirs + (int64_t)p * N);
     const int be = exact_bin_from(h, P.beta, T, bt);
     if (be == bt) return;
+    if (GH) {            // global difference table of the complex (oc), row p
+        if (p < P.d) {
+            unsigned long long *row = oc + (int64_t)p * T;
+            atomicAdd(row + bt, (unsigned long long)(-(long long)cv));
+            atomicAdd(row + be, (unsigned long long)(long long)cv);
+        }
+        return;
+    }
     const uint32_t at = histAddr + ((uint32_t)bt * (uint32_t)Dt + (uint32_t)col) * 4u;
     const uint32_t ae = histAddr + ((uint32_t)be * (uint32_t)Dt + (uint32_t)col) * 4u;
     if (NSPLIT == 1) {
@@ -199,11 +210,11 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
 // lane lists its pairs (bit u * DPL + j of pend) in a per-warp queue of 32 entries, and each lane
 // then fixes one queued pair, whoever found it.  Lanes whose direction meets many exact ties
 // (regular grids seen along axis or diagonal directions) no longer serialise the warp.
-template <int N, int NSPLIT, int DPL>
+template <int N, int NSPLIT, int DPL, bool GH>
 __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow,
                                                  int CP, int i0, int i1, int i2, uint32_t pend, float k0,
                                                  const DirFilter *dirf, int colbase, int pbase, uint32_t histAddr,
-                                                 int Dt, uint32_t HOFF, uint32_t *wq)
+                                                 int Dt, uint32_t HOFF, uint32_t *wq, unsigned long long *oc)
 {
     constexpr int NOCT = 1 << N;
     const int lane = threadIdx.x & 31;
@@ -234,8 +245,8 @@ __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const 
             filter_ceil(k0 + 2.0f * (float)u, f.S0, rf.Glo, rf.Ghi, tlo, thi);
             const int cv = crow[f.oct * CP + i0 + u];
             const int hv = (NSPLIT == 2) ? crow[NOCT * CP + f.oct * CP + i0 + u] : 0;
-            cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col], i0 + u, i1, i2, thi, rf.nr, col, histAddr, Dt, HOFF, cv,
-                                     hv);
+            const int p = (pbase + col < P.d) ? P.perm[pbase + col] : P.d;
+            cubical_fixup<N, NSPLIT, GH>(P, g, p, i0 + u, i1, i2, thi, rf.nr, col, histAddr, Dt, HOFF, cv, hv, oc);
         }
         __syncwarp();
     }
@@ -244,11 +255,12 @@ __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const 
 // One grid row for the DPL directions of each lane.  CLAMP selects the variant whose bins may
 // leave [0, T-1] (heights outside the threshold range); the other variant has been proven
 // in range for the whole row and skips the clamp.
-template <int N, int NSPLIT, int DPL, bool CLAMP>
+template <int N, int NSPLIT, int DPL, bool CLAMP, bool GH>
 __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow, int CP, int L0,
                                         int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
                                         const int (&oct)[DPL], const int (&col)[DPL], int pbase, uint32_t histAddr,
-                                        int Dt, uint32_t HOFF, const DirFilter *dirf, int colbase, uint32_t *wq)
+                                        int Dt, uint32_t HOFF, const DirFilter *dirf, int colbase, uint32_t *wq,
+                                        unsigned long long *const (&orow)[DPL], unsigned long long *oc)
 {
     constexpr int NOCT = 1 << N;
     constexpr int U = (NSPLIT == 1 && DPL <= 2) ? 8 : 4;
@@ -313,6 +325,12 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
 #pragma unroll
             for (int j = 0; j < DPL; ++j) {
                 bad |= tlo[j] ^ thi[j];
+                if constexpr (GH) {
+                    // int64 difference row of this lane's direction in global memory (null for
+                    // an idle column)
+                    if (orow[j]) atomicAdd(orow[j] + clamp_bin(thi[j], rf[j].nr, T), (unsigned long long)(long long)cv[j][u]);
+                    continue;
+                }
                 uint32_t addr;
                 if (!CLAMP) {
                     addr = (uint32_t)thi[j] * D4 + hb[j];
@@ -338,8 +356,8 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                     filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
                     if (tlo != thi) pend |= 1u << (u * DPL + j);
                 }
-            cubical_fixup_block<N, NSPLIT, DPL>(P, g, crow, CP, i0, i1, i2, pend, k0, dirf, colbase, pbase, histAddr, Dt,
-                                                HOFF, wq);
+            cubical_fixup_block<N, NSPLIT, DPL, GH>(P, g, crow, CP, i0, i1, i2, pend, k0, dirf, colbase, pbase, histAddr,
+                                                    Dt, HOFF, wq, oc);
         }
         k0 += 2.0f * (float)U;
         k02 = kk2;
@@ -353,16 +371,21 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             int tlo, thi;
             filter_ceil(k0, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
             const int b = clamp_bin(thi, rf[j].nr, T);
-            const uint32_t addr = histAddr + ((uint32_t)b * (uint32_t)Dt + (uint32_t)col[j]) * 4u;
-            if (NSPLIT == 1) {
-                red_shared_add(addr, cvs);
+            if constexpr (GH) {
+                if (orow[j]) atomicAdd(orow[j] + b, (unsigned long long)(long long)cvs);
             } else {
-                red_shared_add_u32(addr, (uint32_t)cvs);
-                red_shared_add(addr + HOFF, hvs);
+                const uint32_t addr = histAddr + ((uint32_t)b * (uint32_t)Dt + (uint32_t)col[j]) * 4u;
+                if (NSPLIT == 1) {
+                    red_shared_add(addr, cvs);
+                } else {
+                    red_shared_add_u32(addr, (uint32_t)cvs);
+                    red_shared_add(addr + HOFF, hvs);
+                }
             }
-            if (tlo != thi)
-                cubical_fixup<N, NSPLIT>(P, g, P.perm[pbase + col[j]], i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt,
-                                         HOFF, cvs, hvs);
+            if (tlo != thi) {
+                const int p = (pbase + col[j] < P.d) ? P.perm[pbase + col[j]] : P.d;
+                cubical_fixup<N, NSPLIT, GH>(P, g, p, i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF, cvs, hvs, oc);
+            }
         }
         k0 += 2.0f;
     }
@@ -380,14 +403,14 @@ __device__ __forceinline__ void group_sync(int rgroup, int WC)
     }
 }
 
-template <int N, int NSPLIT, int DPL>
+template <int N, int NSPLIT, int DPL, bool GH>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
 {
     constexpr int NOCT = 1 << N;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     const int T = P.T, Dt = P.Dt, CP = P.CP;
-    const int histWords = T * Dt;
+    const int histWords = GH ? 0 : T * Dt;      // GH: no shared histogram
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int WC = Dt / (32 * DPL);         // warps across the direction tile = warps of a row group
@@ -439,6 +462,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         int col[DPL];
 #pragma unroll
         for (int j = 0; j < DPL; ++j) col[j] = wcol * 32 * DPL + j * 32 + lane;
+        // GH: the int64 difference rows of the lane's directions in the complex's output block
+        unsigned long long *const oc = P.out + (int64_t)W.cx * P.d * T;
+        unsigned long long *orow[DPL];
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            const int p = (pbase + col[j] < P.d) ? P.perm[pbase + col[j]] : P.d;
+            orow[j] = (GH && p < P.d) ? oc + (int64_t)p * T : nullptr;
+        }
 
         // ---- each row group walks rows r0 + rgroup, r0 + rgroup + RG, ... with a double-buffered
         // row of octant contributions (one group barrier per row, no block-wide barrier)
@@ -480,18 +511,25 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
                 const float highf = __fadd_ru(__fadd_ru(rf[j].Ghi, A), (float)(rf[j].nr + 1));
                 clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
             }
-            if (__any_sync(0xffffffffu, clampRow))
-                fwd_row<N, NSPLIT, DPL, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF,
-                                              dirf, wcol * 32 * DPL, wq);
-            else
-                fwd_row<N, NSPLIT, DPL, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt, HOFF,
-                                               dirf, wcol * 32 * DPL, wq);
+            if constexpr (GH) {
+                fwd_row<N, NSPLIT, DPL, true, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                                                    HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+            } else {
+                if (__any_sync(0xffffffffu, clampRow))
+                    fwd_row<N, NSPLIT, DPL, true, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                                                         HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+                else
+                    fwd_row<N, NSPLIT, DPL, false, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
+                                                          Dt, HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+            }
         }
         __syncthreads();
-        if (P.direct)
-            cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, P.out + (int64_t)W.cx * P.d * T);
-        else
-            cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, P.out + (int64_t)W.cx * P.d * T);
+        if constexpr (!GH) {
+            if (P.direct)
+                cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
+            else
+                cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
+        }
     }
 }
 
@@ -517,18 +555,18 @@ __global__ void grid_max_abs_kernel(const GridDesc *grids, const double *dirs, i
 
 // The dynamic shared-memory opt-in is set once per kernel instance and size (never inside a
 // stream capture once a size has been seen).
-template <int N, int NSPLIT, int DPL>
+template <int N, int NSPLIT, int DPL, bool GH>
 static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL>,
+        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL, GH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         done = smem;
     }
     if (!launch) return cudaSuccess;
-    cubical_fwd_kernel<N, NSPLIT, DPL><<<grid, kFwdThreads, smem, st>>>(a);
+    cubical_fwd_kernel<N, NSPLIT, DPL, GH><<<grid, kFwdThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -536,29 +574,45 @@ template <int N, int NSPLIT>
 static cudaError_t launch_fwd_d(const CubicalFwdArgs &a, int dpl, int grid, size_t smem, cudaStream_t st, bool launch)
 {
     switch (dpl) {
-    case 1: return launch_fwd_t<N, NSPLIT, 1>(a, grid, smem, st, launch);
-    case 2: return launch_fwd_t<N, NSPLIT, 2>(a, grid, smem, st, launch);
-    default: return launch_fwd_t<N, NSPLIT, 4>(a, grid, smem, st, launch);
+    case 1: return launch_fwd_t<N, NSPLIT, 1, false>(a, grid, smem, st, launch);
+    case 2: return launch_fwd_t<N, NSPLIT, 2, false>(a, grid, smem, st, launch);
+    default: return launch_fwd_t<N, NSPLIT, 4, false>(a, grid, smem, st, launch);
     }
 }
 
-static cudaError_t cubical_fwd_dispatch(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem,
-                                        cudaStream_t st, bool launch)
+// Global-histogram instances: one int32 row plane (the contributions are added as int64), one or
+// two directions per lane.
+template <int N>
+static cudaError_t launch_fwd_gh(const CubicalFwdArgs &a, int dpl, int grid, size_t smem, cudaStream_t st, bool launch)
 {
+    return dpl == 1 ? launch_fwd_t<N, 1, 1, true>(a, grid, smem, st, launch)
+                    : launch_fwd_t<N, 1, 2, true>(a, grid, smem, st, launch);
+}
+
+static cudaError_t cubical_fwd_dispatch(int n, int nsplit, int dpl, bool gh, const CubicalFwdArgs &a, int grid,
+                                        size_t smem, cudaStream_t st, bool launch)
+{
+    if (gh) {
+        if (dpl != 1 && dpl != 2) return cudaErrorInvalidValue;
+        if (n == 1) return launch_fwd_gh<1>(a, dpl, grid, smem, st, launch);
+        if (n == 2) return launch_fwd_gh<2>(a, dpl, grid, smem, st, launch);
+        return launch_fwd_gh<3>(a, dpl, grid, smem, st, launch);
+    }
     if (n == 1) return nsplit == 1 ? launch_fwd_d<1, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<1, 2>(a, dpl, grid, smem, st, launch);
     if (n == 2) return nsplit == 1 ? launch_fwd_d<2, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<2, 2>(a, dpl, grid, smem, st, launch);
     return nsplit == 1 ? launch_fwd_d<3, 1>(a, dpl, grid, smem, st, launch) : launch_fwd_d<3, 2>(a, dpl, grid, smem, st, launch);
 }
 
-cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st)
+cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, bool gh, const CubicalFwdArgs &a, int grid, size_t smem,
+                               cudaStream_t st)
 {
-    return cubical_fwd_dispatch(n, nsplit, dpl, a, grid, smem, st, true);
+    return cubical_fwd_dispatch(n, nsplit, dpl, gh, a, grid, smem, st, true);
 }
 
-cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem)
+cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, bool gh, size_t smem)
 {
     CubicalFwdArgs a{};
-    return cubical_fwd_dispatch(n, nsplit, dpl, a, 1, smem, nullptr, false);
+    return cubical_fwd_dispatch(n, nsplit, dpl, gh, a, 1, smem, nullptr, false);
 }
 
 int cubical_fwd_pitch(int maxL0)
@@ -567,8 +621,13 @@ int cubical_fwd_pitch(int maxL0)
     return ((L0p + 31) & ~31) + 4;        // words; = 4 mod 32: octant planes on distinct bank groups
 }
 
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0)
+// gh: no shared histogram (the global-histogram variant, one row plane).
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh)
 {
+    if (gh) {
+        nsplit = 1;
+        T = 0;
+    }
     const int noct = 1 << n;
     const int WC = Dt / (32 * dpl);
     const int RG = (kFwdThreads / 32) / WC;

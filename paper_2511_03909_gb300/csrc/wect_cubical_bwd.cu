@@ -130,8 +130,12 @@ __device__ __forceinline__ int rsum_group(uint32_t e, int gi, bool clampg, F2 KA
 // An octant sum as two int32 halves, value = hi * 2^32 + lo with lo the signed low word (so hi
 // is the high word plus one when lo < 0).  The routing kernel then multiplies each half by its
 // small coefficient with one 32 x 32 -> 64 multiply-add.  |value| < 2^63 / 3^n keeps hi in range.
-__device__ __forceinline__ void store_split(int64_t *p, long long v)
+__device__ __forceinline__ void store_split(int64_t *p, long long v, bool accumulate)
 {
+    if (accumulate) {            // a later direction chunk: add to the stored sum
+        const int2 old = *reinterpret_cast<const int2 *>(p);
+        v += (long long)(((unsigned long long)(long long)old.y << 32) + (unsigned long long)(long long)old.x);
+    }
     const int lo = (int)(unsigned int)((unsigned long long)v & 0xffffffffull);
     const int hi = (int)((v - (long long)lo) >> 32);
     *reinterpret_cast<int2 *>(p) = make_int2(lo, hi);
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
     const GridDesc g = P.grids[W.cx];
     const int L0 = g.L[0], L1 = g.L[1];
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
-    const long long *S = reinterpret_cast<const long long *>(P.S) + (int64_t)W.cx * d * T;
+    const long long *S = reinterpret_cast<const long long *>(P.S) + ((int64_t)W.cx * P.d_all + P.p0) * T;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
 
     if (tid == 0) {
@@ -287,8 +291,8 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
                         }
                     }
                 }
-                if (liveA) store_split(P.Rv + (int64_t)o * P.total_nv + voutA, accA);
-                if (liveB) store_split(P.Rv + (int64_t)o * P.total_nv + voutA + 32, accB);
+                if (liveA) store_split(P.Rv + (int64_t)o * P.total_nv + voutA, accA, P.accumulate != 0);
+                if (liveB) store_split(P.Rv + (int64_t)o * P.total_nv + voutA + 32, accB, P.accumulate != 0);
             }
         }
     }
@@ -472,24 +476,31 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
 
 // ------------------------------------------------------------------ launchers
 
-cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
+cudaError_t launch_cubical_bwd_rsum(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st)
 {
     cudaError_t e;
-    const int blocks = (int)((a.v_end - a.v_begin + 255) / 256);
-    if (n_items <= 0 || blocks <= 0) return cudaSuccess;
-#define BWD(NN)                                                                                                \
+    if (n_items <= 0) return cudaSuccess;
+#define RS(NN)                                                                                                 \
     do {                                                                                                       \
         e = cudaFuncSetAttribute(cubical_bwd_rsum_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                  (int)smem_rsum);                                                              \
         if (e != cudaSuccess) return e;                                                                        \
         cubical_bwd_rsum_kernel<NN><<<n_items, 1024, smem_rsum, st>>>(a);                                      \
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;                                                 \
-        cubical_bwd_route_kernel<NN><<<blocks, 256, 0, st>>>(a);                                               \
     } while (0)
-    if (n == 1) BWD(1);
-    else if (n == 2) BWD(2);
-    else BWD(3);
-#undef BWD
+    if (n == 1) RS(1);
+    else if (n == 2) RS(2);
+    else RS(3);
+#undef RS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cubical_bwd_route(int n, const CubicalBwdArgs &a, cudaStream_t st)
+{
+    const int blocks = (int)((a.v_end - a.v_begin + 255) / 256);
+    if (blocks <= 0) return cudaSuccess;
+    if (n == 1) cubical_bwd_route_kernel<1><<<blocks, 256, 0, st>>>(a);
+    else if (n == 2) cubical_bwd_route_kernel<2><<<blocks, 256, 0, st>>>(a);
+    else cubical_bwd_route_kernel<3><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

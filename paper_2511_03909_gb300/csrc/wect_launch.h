@@ -46,6 +46,10 @@ struct CubicalBwdArgs {
     int frac_bits;
     int64_t total_nv;
     int64_t uniform_nv;           // vertex count shared by every grid (0 when they differ)
+    // direction chunks of the octant sums (d x T larger than the shared suffix table): dirs, d,
+    // perm and octb describe the chunk, whose rows start at direction p0 of the d_all rows of S;
+    // accumulate adds the chunk's sums to Rv instead of storing them
+    int d_all, p0, accumulate;
 };
 
 struct SimplexFwdArgs {
@@ -83,12 +87,17 @@ constexpr int kStageBytes = kWinBytes + kIdBytes + kWtBytes;
 static_assert(kWinBytes % 16 == 0 && kIdBytes % 16 == 0 && kWtBytes % 16 == 0, "16-byte stage pieces");
 
 // cubical
-cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st);
-cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, size_t smem);   // dynamic smem attribute, outside capture
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0);
+// gh selects the global-histogram variant (large T): every update goes to the int64 difference
+// table in global memory; it needs items that are not scanned in the CTA (direct = 0).
+cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, bool gh, const CubicalFwdArgs &a, int grid, size_t smem,
+                               cudaStream_t st);
+cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, bool gh, size_t smem);   // dynamic smem attribute, outside capture
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh = false);
 int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
-cudaError_t launch_cubical_bwd(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
+// The adjoint's octant sums for one direction chunk, then (once every chunk is summed) the routing.
+cudaError_t launch_cubical_bwd_rsum(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
+cudaError_t launch_cubical_bwd_route(int n, const CubicalBwdArgs &a, cudaStream_t st);
 size_t cubical_bwd_rsum_smem(int n, int d, int T, int R);
 // ECF kernels for nf filters: bins [nf][nv], out [nf][T] (blockIdx.y = filter).
 cudaError_t launch_cubical_ecf(int n, const GridDesc *grids, const uint16_t *bins, int T, int weighted,
@@ -105,7 +114,9 @@ cudaError_t launch_coords_to_f32(const double *x, int64_t n, float *xf, cudaStre
 cudaError_t launch_vertex_bins(int n, const double *coords, const float *xf, int64_t nv, const double *dirs,
                                const float *tab, int d, int dtile, int Dt, int T, const double *beta, uint16_t *bins,
                                cudaStream_t st);
-cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st);
+// gh: every signed weight goes to the int64 difference table in global memory (no shared
+// histogram; any T).
+cudaError_t launch_simplex_fwd(int nsplit, bool gh, const SimplexFwdArgs &a, int grid, cudaStream_t st);
 // Vertex bins of a 32-direction tile fused with the vertices' own scatter (a: the list of dim 0).
 cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, const double *coords, const float *xf,
                                   int64_t nv, const double *dirs, const float *tab, const double *beta, uint16_t *bins,

@@ -118,9 +118,12 @@ __device__ __forceinline__ T ld_ro(const T *p)
 // weights and the bins (a window of chunk vertices) are in shared memory.  bins and histLane
 // already carry the lane's column; the max of the vertex bins (Eq. "msi") selects the histogram
 // row.
-template <int NSPLIT, int M, int GS, bool FULL, bool SMEM, typename IdT>
+// With GH the signed weight goes straight to the lane's int64 difference row orow in global memory
+// (null for a padding column) instead of the shared histogram.
+template <int NSPLIT, int M, int GS, bool FULL, bool SMEM, typename IdT, bool GH = false>
 __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vbase, const int2 *__restrict__ wp, int n,
-                                             const uint16_t *__restrict__ bins, uint32_t histLane, uint32_t HOFF)
+                                             const uint16_t *__restrict__ bins, uint32_t histLane, uint32_t HOFF,
+                                             unsigned long long *orow = nullptr)
 {
     int vid[GS][M];
     int2 w[GS];
@@ -189,9 +192,15 @@ __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vb
     }
 #pragma unroll
     for (int g = 0; g < GS; ++g) {
-        const uint32_t addr = histLane + (uint32_t)bin[g] * 128u;
-        red_shared_add(addr, w[g].x);
-        if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+        if constexpr (GH) {
+            // packed {v, 0} or {low 16 bits, v >> 16}: v = (w.y << 16) + w.x either way
+            if (orow && (FULL || g < n))
+                atomicAdd(orow + bin[g], (unsigned long long)(((long long)w[g].y << 16) + (long long)w[g].x));
+        } else {
+            const uint32_t addr = histLane + (uint32_t)bin[g] * 128u;
+            red_shared_add(addr, w[g].x);
+            if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+        }
     }
 }
 
@@ -222,7 +231,9 @@ constexpr int kGatherGS = 8;
 
 // Gather for one 32-direction tile straight from the global bin table: CTAs take chunks of
 // P.chunk simplices (at most the flush bound), warps take groups of kGatherGS simplices.
-template <int NSPLIT, int M>
+// GH: no shared histogram; every signed weight is added to the int64 difference table in global
+// memory (T beyond shared memory).
+template <int NSPLIT, int M, bool GH>
 __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const SimplexFwdArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -232,8 +243,12 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const S
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t histLane = smem_addr(hist) + (uint32_t)lane * 4u;
     const uint32_t HOFF = (uint32_t)T * 128u;
-    for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
+    const int p = P.dtile * 32 + lane;
+    unsigned long long *orow = (GH && p < P.d) ? P.out + (int64_t)p * T : nullptr;
+    if (!GH) {
+        for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+    }
     const uint16_t *bins = P.bins + lane;
     const int64_t nchunks = (P.k + P.chunk - 1) / P.chunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -242,11 +257,13 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const S
             const int n = (int)(b1 - bb < (int64_t)GS ? b1 - bb : (int64_t)GS);
             const int32_t *ids = (M == 1) ? nullptr : P.simp + bb * M;
             if (n == GS)
-                gather_group<NSPLIT, M, GS, true, false>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF);
+                gather_group<NSPLIT, M, GS, true, false, int32_t, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
+                                                                      orow);
             else
-                gather_group<NSPLIT, M, GS, false, false>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF);
+                gather_group<NSPLIT, M, GS, false, false, int32_t, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
+                                                                       orow);
         }
-        simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
+        if (!GH) simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
     }
 }
 
@@ -866,16 +883,16 @@ cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, co
 
 size_t simplex_fwd_smem(int nsplit, int T, int Dt) { return (size_t)nsplit * T * Dt * 4u; }
 
-template <int NSPLIT>
+template <int NSPLIT, bool GH>
 static cudaError_t launch_simplex_fwd_s(const SimplexFwdArgs &a, int grid, cudaStream_t st)
 {
-    const size_t sm = simplex_fwd_smem(NSPLIT, a.T, a.Dt);
+    const size_t sm = GH ? 0 : simplex_fwd_smem(NSPLIT, a.T, a.Dt);
     cudaError_t e = cudaSuccess;
-#define SF(MM)                                                                                                  \
-    do {                                                                                                        \
-        e = cudaFuncSetAttribute(simplex_fwd_kernel<NSPLIT, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 (int)sm);                                                                      \
-        if (e == cudaSuccess) simplex_fwd_kernel<NSPLIT, MM><<<grid, kSimplexThreads, sm, st>>>(a);            \
+#define SF(MM)                                                                                                      \
+    do {                                                                                                            \
+        e = cudaFuncSetAttribute(simplex_fwd_kernel<NSPLIT, MM, GH>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)sm);                                                                          \
+        if (e == cudaSuccess) simplex_fwd_kernel<NSPLIT, MM, GH><<<grid, kSimplexThreads, sm, st>>>(a);            \
     } while (0)
     switch (a.m) {
     case 1: SF(1); break;
@@ -888,10 +905,11 @@ static cudaError_t launch_simplex_fwd_s(const SimplexFwdArgs &a, int grid, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_simplex_fwd(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st)
+cudaError_t launch_simplex_fwd(int nsplit, bool gh, const SimplexFwdArgs &a, int grid, cudaStream_t st)
 {
     if (a.Dt != 32 || !a.swp) return cudaErrorInvalidValue;
-    return nsplit == 1 ? launch_simplex_fwd_s<1>(a, grid, st) : launch_simplex_fwd_s<2>(a, grid, st);
+    if (gh) return launch_simplex_fwd_s<1, true>(a, grid, st);
+    return nsplit == 1 ? launch_simplex_fwd_s<1, false>(a, grid, st) : launch_simplex_fwd_s<2, false>(a, grid, st);
 }
 
 cudaError_t launch_pack_weights(const int64_t *sw, int64_t k, int sign, int nsplit, int2 *out, cudaStream_t st)

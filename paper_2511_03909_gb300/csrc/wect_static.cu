@@ -133,7 +133,7 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
     const int nsplit = 1;
     const int64_t climit = (int64_t(1) << n) * 255;
     const int kflush = (int)((((int64_t)1 << 31) - 1) / climit);
-    if (L[0] > kflush) return sfail(WECT_ERR_UNSUPPORTED, "grid rows too long");
+    if (L[0] > kflush) return sfail(WECT_ERR_UNSUPPORTED, "grid rows too long");     // (2^31 - 1) / (2^n 255)
 
     // tile shape: widest direction tile, then most directions per lane, that fits shared memory
     int dev = 0, sms = 1, optin = 48 * 1024, per_sm = 100 * 1024;
@@ -156,7 +156,15 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
             smem = sm;
             break;
         }
-    if (!dpl) return sfail(WECT_ERR_UNSUPPORTED, "T too large for the shared-memory histogram");
+    bool gh = false;
+    if (!dpl) {
+        // no shared histogram fits this T: scatter into the int64 table in global memory
+        gh = true;
+        Dt = std::min(Dmax, 256);
+        dpl = Dt >= 64 ? 2 : 1;
+        smem = cubical_fwd_smem(n, nsplit, dpl, T, Dt, L[0], true);
+        if (smem > (size_t)optin - 1024) return sfail(WECT_ERR_UNSUPPORTED, "grid rows too long for the row buffers");
+    }
     const int ctas = sms * std::max(1, std::min((int)(per_sm / (smem + 2048)), 2048 / threads));
     const int rows = L[1] * L[2];
     const int ntiles = (d + Dt - 1) / Dt;
@@ -222,7 +230,7 @@ extern "C" wect_status wect_cubical_compute_static(int n, const int64_t *dims, c
     a.climit = climit;
     a.direct = 0;
     a.out = reinterpret_cast<unsigned long long *>(out);
-    SCK(launch_cubical_fwd(n, nsplit, dpl, a, std::min(ctas, a.n_items), smem, st));
+    SCK(launch_cubical_fwd(n, nsplit, dpl, gh, a, std::min(ctas, a.n_items), smem, st));
     SCK(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), d, T, st));
 #undef SCK
     return WECT_OK;

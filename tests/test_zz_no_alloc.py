@@ -39,6 +39,7 @@ CASES = [
     ([70, 45], 64, 64, -SQ2, SQ2, True, 13, True),                       # n = 2
     ([37, 29], 40, 33, -SQ2, SQ2, False, 14, True),                      # unweighted (WECT_W_ONE)
     ([9, 8, 7], 33, 17, -0.4, 0.3, True, 15, True),                      # narrow range
+    ([23, 19, 7], 50, 4096, -SQ3, SQ3, True, 16, True),                  # T beyond the shared histogram
 ]
 
 
