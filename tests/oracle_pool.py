@@ -95,6 +95,18 @@ def volume_adjoint(vw: np.ndarray, tw: np.ndarray, dims, dirs, T: int, lo: float
     return W, B, g
 
 
+def ecf_filter(dims, seed: int) -> np.ndarray:
+    """Uniform [0, 1) float64 vertex filter of a grid (an intensity image or volume)."""
+    return np.random.default_rng(seed).random(int(np.prod(dims)))
+
+
+def ecf_grid(dims, seed: int, T: int) -> np.ndarray:
+    """Unweighted ECF of the full cubical grid for the filter ecf_filter(dims, seed) over [0, 1]."""
+    O = _O()
+    nv = int(np.prod(dims))
+    return O.wecf_cubical(dims, np.zeros(nv, dtype=np.int64), ecf_filter(dims, seed), T, 0.0, 1.0, weighted=False)[0]
+
+
 def _noop(k):
     return k
 

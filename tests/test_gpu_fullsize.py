@@ -11,7 +11,9 @@ element by element (all results are exact integers, the adjoint's float32 is exa
   the same two, and the autograd gradient of the mean squared error over the whole batch for
   both (all 128 directions against the oracle's exact adjoint); plus central finite differences
   of the GPU forward at h = 1e-3 on tie-free vertices.
-- 64^2 image, d = 32, T = 64 and its ECF are covered completely in test_gpu_cubical.py.
+- 64^2 image, d = 32, T = 64 and its ECF are covered completely in test_gpu_cubical.py;
+- the intensity-filter ECF at the paper's throughput sizes 2048^2 and 128^3, T = 1000 and 10000,
+  uniform [0, 1) filters over [0, 1], through the same call the benchmark times.
 
 The oracle runs in spawned worker processes, one per host core; all its work is submitted when
 the module starts so that it overlaps the GPU work.
@@ -23,11 +25,12 @@ import pytest
 
 import synthetic as S
 from gpu_common import cuda, dev, lib, torch
-from oracle_pool import OraclePool, images, mesh_dirs, voxel_dirs, volume_adjoint
+from oracle_pool import OraclePool, ecf_filter, ecf_grid, images, mesh_dirs, voxel_dirs, volume_adjoint
 
 pytestmark = pytest.mark.gpu
 
 VOL_CHECKED = (17, 200)          # volumes of the differentiation batch compared with the oracle
+ECF_CASES = [([2048, 2048], 10000), ([128, 128, 128], 10000), ([2048, 2048], 1000), ([128, 128, 128], 1000)]
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +43,9 @@ def P():
 def jobs(P):
     pool = OraclePool()
     J = {}
-    # the longest single tasks first: one volume's transform, target and adjoint each
+    # the longest single tasks first: the T = 10000 ECFs (the oracle counts thresholds one by
+    # one), then one volume's transform, target and adjoint each
+    J["ecf"] = [pool.submit(ecf_grid, dims, 70 + i, T) for i, (dims, T) in enumerate(ECF_CASES)]
     wv = S.volume_batch_diff()
     from oracle import oracle as O
 
@@ -184,3 +189,15 @@ def test_images2d_4096_every_image(P, jobs):
     got = got.cpu().numpy()
     ref = np.stack([r for j in jobs["images"] for r in j.get()])
     assert np.array_equal(got, ref)
+
+
+def test_ecf_intensity_paper_sizes(P, jobs):
+    """The unweighted ECF of uniform images and volumes, the filter being the intensity, through
+    ecf_compute as the benchmark's ECF rows call it."""
+    for i, (dims, T) in enumerate(ECF_CASES):
+        f = cuda(ecf_filter(dims, 70 + i))
+        cx = P.CubicalComplex(None, dims=dims)
+        out = torch.empty(10000, dtype=torch.int64, device=f.device)
+        got = cx.ecf(f, T, 0.0, 1.0, out=out[:T]).cpu().numpy()
+        cx.device_status()
+        assert np.array_equal(got, jobs["ecf"][i].get()), (dims, T)
