@@ -497,3 +497,64 @@ def test_grid_default_range_with_rounding(oracle, dims):
             M = max(M, abs(height_reading(x, list(s))))
     lo, hi = oracle.default_range_grid(dims, np.ascontiguousarray(dirs))
     assert hi == M and lo == -M
+
+
+# ----------------------------------------------------------------------- four dimensions
+
+
+def test_four_sphere_and_four_box_closed_forms(oracle):
+    """R^4: the boundary of the 5-simplex (all 4-faces of 6 points in general position, and their
+    faces) is a 4-sphere, Euler characteristic 1 - 1 + 1 - 1 + 1 ... = 2; the Freudenthal
+    triangulation of a 3 x 2 x 2 x 2 grid is a triangulated box, Euler characteristic 1.  Both at
+    the top threshold, in every direction."""
+    rng = np.random.default_rng(61)
+    pts = rng.uniform(-1, 1, (6, 4))
+    from itertools import combinations
+
+    top = np.array(list(combinations(range(6), 5)), dtype=np.int64)
+    sphere = S.closure_from_top(pts, top)
+    assert [len(s) for s in sphere.simplices] == [15, 20, 15, 6]
+    dirs = S.random_directions(7, 4, seed=62)
+    one = oracle.simplicial_weights(sphere.simplices, np.ones(6, dtype=np.int64), "one")
+    assert np.all(oracle.wect_simplicial(pts, sphere.simplices, one, dirs, 9)[:, -1] == 2)
+    dims = [3, 2, 2, 2]
+    lists = S.freudenthal_lists(dims)
+    assert len(lists) == 4 and lists[3].shape == (2 * 24, 5)
+    X = oracle.grid_coords(dims)
+    one = oracle.simplicial_weights(lists, np.ones(X.shape[0], dtype=np.int64), "one")
+    assert np.all(oracle.wect_simplicial(X, lists, one, dirs, 9)[:, -1] == 1)
+
+
+@pytest.mark.parametrize("dyadic", [True, False])
+def test_brute_force_four_dimensional(oracle, dyadic):
+    """A jittered 2^4 Freudenthal grid in R^4 (24 four-simplices and their faces), u8 weights:
+    the oracle equals brute-force enumeration of the sublevel subcomplexes, in exact rational
+    arithmetic for dyadic coordinates and directions, else with float64 heights from the
+    independent restatement of the rounding rule."""
+    dims = [2, 2, 2, 2]
+    rng = np.random.default_rng(63 + dyadic)
+    lists = S.freudenthal_lists(dims)
+    base = oracle.grid_coords(dims)
+    if dyadic:
+        X = base + rng.integers(-2, 3, base.shape).astype(np.float64) / 16.0
+        dirs = rng.integers(-8, 9, size=(5, 4)).astype(np.float64) / 8.0
+    else:
+        X = base + rng.uniform(-0.2, 0.2, base.shape)
+        dirs = S.random_directions(5, 4, seed=64)
+    nv = X.shape[0]
+    vw = rng.integers(0, 256, nv).astype(np.int64)
+    cx = S.Simplicial(coords=np.ascontiguousarray(X), simplices=lists, weights=vw.astype(np.uint8))
+    T, lo, hi = 17, -2.0, 2.0                     # step 1/4: the float64 thresholds are exact too
+    got = oracle.wect_simplicial(X, lists, oracle.simplicial_weights(lists, vw), dirs, T, lo, hi)
+    faces, weights = simplicial_faces(cx, vw)
+    if dyadic:
+        beta = [Fraction(lo) + q * (Fraction(hi) - Fraction(lo)) / (T - 1) for q in range(T)]
+    else:
+        step = (hi - lo) / (T - 1)
+        beta = [lo + q * step for q in range(T)]
+    for p in range(len(dirs)):
+        if dyadic:
+            f = [sum(Fraction(X[v, a]) * Fraction(dirs[p, a]) for a in range(4)) for v in range(nv)]
+        else:
+            f = [height_reading(list(X[v]), list(dirs[p])) for v in range(nv)]
+        assert got[p].tolist() == brute_wecf(nv, faces, weights, f, T, beta)
