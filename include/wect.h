@@ -109,11 +109,11 @@ WECT_API wect_status wect_complex_create_freudenthal(int n, const int64_t *dims,
 
 /*
  * Geometric simplicial complex in R^n (Section 3 "inputs": per dimension a list of vertex
- * index rows and a weight per simplex).
- *   n                ambient dimension, 1..3
+ * index rows and a weight per simplex; Section 2: the method holds in any R^n).
+ *   n                ambient dimension, 1..4
  *   n_vertices       k_0 >= 1
  *   coords (dev)     [k_0][n] float64 vertex positions l(v), finite
- *   max_dim          highest simplex dimension present, 0..3
+ *   max_dim          highest simplex dimension present, 0..4
  *   counts (host)    [max_dim+1], counts[0] = k_0, counts[i] = k_i >= 0
  *   simplices (host) [max_dim+1] device pointers; simplices[i] (i >= 1) is int32 [k_i][i+1],
  *                    each index in [0, k_0); simplices[0] is ignored.  Closure under faces
@@ -143,8 +143,8 @@ WECT_API wect_status wect_complex_set_weights(wect_complex cx, const void *verte
 /* Number of vertices k_0 (0 for a NULL handle). */
 WECT_API int64_t wect_complex_num_vertices(wect_complex cx);
 
-/* Number of cells of each dimension (host array of 4, zero beyond the top dimension). */
-WECT_API wect_status wect_complex_cell_counts(wect_complex cx, int64_t *counts4);
+/* Number of cells of each dimension 0..4 (host array of 5, zero beyond the top dimension). */
+WECT_API wect_status wect_complex_cell_counts(wect_complex cx, int64_t *counts5);
 
 /* Synchronise the stream, return and clear the device status word of the complex. */
 WECT_API wect_status wect_complex_device_status(wect_complex cx, wect_stream stream);

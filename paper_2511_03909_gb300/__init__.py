@@ -197,7 +197,7 @@ class _Complex:
         return self._h
 
     def cell_counts(self):
-        buf = (C.c_int64 * 4)()
+        buf = (C.c_int64 * 5)()
         _check(load().wect_complex_cell_counts(self._h, buf))
         return [int(x) for x in buf]
 

@@ -217,20 +217,20 @@ struct wect_complex_s {
     int nsplit = 1;
     int64_t climit = 0;            // cubical: max |c_o(v)|; simplicial: max |w(s)|
     int kflush = 1 << 16;
-    int64_t cells[4] = {0, 0, 0, 0};
+    int64_t cells[kMaxSimplexDim + 1] = {};
     // simplicial
     double *d_coords = nullptr;
     float *d_xf = nullptr;         // float32 copies of the coordinates (round to nearest)
     int max_dim = 0;
-    int64_t counts[4] = {0, 0, 0, 0};
-    int32_t *d_simp[4] = {nullptr, nullptr, nullptr, nullptr};
-    int64_t *d_sw[4] = {nullptr, nullptr, nullptr, nullptr};   // d_sw[0] = vertex weights (fixed)
+    int64_t counts[kMaxSimplexDim + 1] = {};
+    int32_t *d_simp[kMaxSimplexDim + 1] = {};
+    int64_t *d_sw[kMaxSimplexDim + 1] = {};            // d_sw[0] = vertex weights (fixed)
     // staged gather: per list of dim >= 1, chunk-local ids and per-chunk vertex lists
-    int2 *d_swp[4] = {nullptr, nullptr, nullptr, nullptr};    // packed signed weights of the gather
-    uint16_t *d_local[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t *d_cverts[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t *d_cnu[4] = {nullptr, nullptr, nullptr, nullptr};
-    int64_t nchunks[4] = {0, 0, 0, 0};
+    int2 *d_swp[kMaxSimplexDim + 1] = {};              // packed signed weights of the gather
+    uint16_t *d_local[kMaxSimplexDim + 1] = {};
+    int32_t *d_cverts[kMaxSimplexDim + 1] = {};
+    int32_t *d_cnu[kMaxSimplexDim + 1] = {};
+    int64_t nchunks[kMaxSimplexDim + 1] = {};
     int sw_mode = WECT_SW_MAX_OF_VERTICES;
     // device state
     int *d_status = nullptr;
@@ -484,7 +484,7 @@ static wect_status ensure_common_ws(Workspace &ws, int T, int d = 1)
 {
     CK(ws.perm.ensure((size_t)d), "alloc");
     CK(ws.octb.ensure(9), "alloc");
-    CK(ws.range.ensure(6), "alloc");
+    CK(ws.range.ensure(8), "alloc");      // lo, hi, step, max |x_a| for a < n <= 4, spare
     CK(ws.beta.ensure((size_t)T), "alloc");
     CK(ws.M.ensure(2), "alloc");
     CK(ws.counter.ensure(1), "alloc");
@@ -618,9 +618,9 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
 {
     if (!out) return fail(WECT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (n < 1 || n > 3) return fail(WECT_ERR_INVALID_ARG, "n must be 1..3 (got %d)", n);
+    if (n < 1 || n > kMaxSimplexN) return fail(WECT_ERR_INVALID_ARG, "n must be 1..%d (got %d)", kMaxSimplexN, n);
     if (n_vertices < 1 || n_vertices >= (1ll << 31)) return fail(WECT_ERR_INVALID_ARG, "n_vertices out of range");
-    if (max_dim < 0 || max_dim > 3) return fail(WECT_ERR_INVALID_ARG, "max_dim must be 0..3");
+    if (max_dim < 0 || max_dim > kMaxSimplexDim) return fail(WECT_ERR_INVALID_ARG, "max_dim must be 0..%d", kMaxSimplexDim);
     if (!coords || !counts) return fail(WECT_ERR_INVALID_ARG, "coords/counts is NULL");
     if (counts[0] != n_vertices) return fail(WECT_ERR_INVALID_ARG, "counts[0] must equal n_vertices");
     if (sw_mode != WECT_SW_MAX_OF_VERTICES && sw_mode != WECT_SW_EXPLICIT)
@@ -669,7 +669,7 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
     // per-axis max |x| into range[3..5]
     std::vector<unsigned long long> zeros(3, 0ull);
     unsigned long long *d_xm = reinterpret_cast<unsigned long long *>(c->ws.range.p + 3);
-    if ((e = cudaMemsetAsync(c->ws.range.p, 0, 6 * sizeof(double), st))) return cleanup(cuda_fail(e, "memset"));
+    if ((e = cudaMemsetAsync(c->ws.range.p, 0, 8 * sizeof(double), st))) return cleanup(cuda_fail(e, "memset"));
     for (int a = 0; a < n; ++a) {
         if ((e = launch_max_abs_f64(c->d_coords, n_vertices, n, a, d_xm + a, st))) return cleanup(cuda_fail(e, "max_abs"));
         g_launches++;
@@ -716,7 +716,7 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
     }
     int bad[4] = {0, 0, 0, 0};
     unsigned long long wmax = 0;
-    double xm[3] = {0, 0, 0};
+    double xm[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaMemcpyAsync(&wmax, c->ws.M.p, sizeof wmax, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaMemcpyAsync(xm, c->ws.range.p + 3, sizeof xm, cudaMemcpyDeviceToHost, st)) ||
@@ -774,7 +774,7 @@ extern "C" void wect_complex_destroy(wect_complex c)
     if (c->d_xg) cudaFree(c->d_xg);
     if (c->d_coords) cudaFree(c->d_coords);
     if (c->d_xf) cudaFree(c->d_xf);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i <= kMaxSimplexDim; ++i) {
         if (c->d_simp[i]) cudaFree(c->d_simp[i]);
         if (c->d_sw[i]) cudaFree(c->d_sw[i]);
         if (c->d_swp[i]) cudaFree(c->d_swp[i]);
@@ -790,10 +790,10 @@ extern "C" void wect_complex_destroy(wect_complex c)
 
 extern "C" int64_t wect_complex_num_vertices(wect_complex c) { return c ? c->nv : 0; }
 
-extern "C" wect_status wect_complex_cell_counts(wect_complex c, int64_t *counts4)
+extern "C" wect_status wect_complex_cell_counts(wect_complex c, int64_t *counts5)
 {
-    if (!c || !counts4) return fail(WECT_ERR_INVALID_ARG, "NULL argument");
-    for (int i = 0; i < 4; ++i) counts4[i] = c->cells[i];
+    if (!c || !counts5) return fail(WECT_ERR_INVALID_ARG, "NULL argument");
+    for (int i = 0; i <= kMaxSimplexDim; ++i) counts5[i] = c->cells[i];
     return WECT_OK;
 }
 
@@ -1156,7 +1156,7 @@ extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, 
     CK(c->ws.Iacc.ensure((size_t)c->nv * 2), "alloc Iacc");
     if ((s = simplicial_range(c, dirs, d, T, lo, hi, st))) return s;
     KL(launch_suffix_rows(dW, c->ws.S.p, d, T, INT64_MAX / d, c->d_status, st), "suffix_rows");
-    const int32_t *simp[4] = {nullptr, c->d_simp[1], c->d_simp[2], c->d_simp[3]};
+    const int32_t *simp[kMaxSimplexDim + 1] = {nullptr, c->d_simp[1], c->d_simp[2], c->d_simp[3], c->d_simp[4]};
     CK(launch_simplicial_bwd(c->n, c->d_coords, c->d_xf, c->nv, simp, c->counts, c->max_dim, c->d_sw[0], dirs, d, T, c->ws.dtab.p,
                              c->ws.beta.p, c->ws.S.p, c->ws.bins.p, c->ws.Iacc.p, grad_w, scale, st),
        "simplicial_bwd");

@@ -18,7 +18,9 @@ namespace wect {
 
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int32_t kMagicBits = 0x4B400000;     // bit pattern of kMagic
-constexpr int kMaxN = 3;
+constexpr int kMaxN = 3;              // grid dimension (cubical complexes)
+constexpr int kMaxSimplexN = 4;       // ambient dimension of simplicial complexes
+constexpr int kMaxSimplexDim = 4;     // top simplex dimension of simplicial complexes
 
 // device status word bits
 constexpr int kStatusOverflow = 1;
@@ -72,6 +74,16 @@ __device__ __forceinline__ double height3(double x0, double x1, double x2, const
     if (N == 1) return __dmul_rn(x0, s[0]);
     if (N == 2) return __fma_rn(x0, s[0], __dmul_rn(x1, s[1]));
     return __fma_rn(x0, s[0], __fma_rn(x1, s[1], __dmul_rn(x2, s[2])));
+}
+
+// The same rule for N coordinates in an array (simplicial complexes, N <= 4).
+template <int N>
+__device__ __forceinline__ double heightv(const double *x, const double *s)
+{
+    double h = __dmul_rn(x[N - 1], s[N - 1]);
+#pragma unroll
+    for (int c = N - 2; c >= 0; --c) h = __fma_rn(x[c], s[c], h);
+    return h;
 }
 
 // Exact bin of h against the float64 threshold table, starting from a nearby candidate.

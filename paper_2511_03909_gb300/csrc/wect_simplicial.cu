@@ -22,8 +22,9 @@ constexpr int kSimplexThreads = 512;
 
 // Per direction p, the float32 form u = sum_a x~_a A_a + C of the threshold coordinate
 // (h - lo) / step, with x~_a = rn32(x_a), A_a = rn32(s_a / step), C = rn32(-lo / step), and a bound
-// eta on |u - (h - lo) / step| (Sec. 3.2, the bin of a vertex height).  tab[p] = {A_0, A_1, A_2, C,
-// eta, 0, 0, 0}.  A zero step (lo == hi) gives eta = inf, so every bin goes to the float64 path.
+// eta on |u - (h - lo) / step| (Sec. 3.2, the bin of a vertex height).  tab[p] = {A_0, A_1, A_2,
+// A_3, C, eta, 0, 0} (A_a = 0 for a >= N).  A zero step (lo == hi) gives eta = inf, so every bin
+// goes to the float64 path.
 template <int N>
 __global__ void dir_filter_kernel(const double *__restrict__ dirs, int d, int T, const double *__restrict__ range,
                                   float *__restrict__ tab)
@@ -31,7 +32,7 @@ __global__ void dir_filter_kernel(const double *__restrict__ dirs, int d, int T,
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= d) return;
     const double lo = range[0], step = range[2];
-    float Af[3] = {0.f, 0.f, 0.f}, Cf = 0.f, eta = __int_as_float(0x7f800000);
+    float Af[4] = {0.f, 0.f, 0.f, 0.f}, Cf = 0.f, eta = __int_as_float(0x7f800000);
     double U = 0.0;
     if (step > 0.0) {
         U = fabs(lo) / step;
@@ -48,12 +49,12 @@ __global__ void dir_filter_kernel(const double *__restrict__ dirs, int d, int T,
     // |u| <= U: beyond 2^21 (or a zero step) the magic-constant ceiling is not sound, so every
     // bin takes the exact path (u = 0, eta = inf)
     if (!(step > 0.0) || !(U + (double)T <= 0x1p21)) {
-        Af[0] = Af[1] = Af[2] = Cf = 0.f;
+        Af[0] = Af[1] = Af[2] = Af[3] = Cf = 0.f;
         eta = __int_as_float(0x7f800000);
     }
     float4 *t = reinterpret_cast<float4 *>(tab + (int64_t)p * 8);
-    t[0] = make_float4(Af[0], Af[1], Af[2], Cf);
-    t[1] = make_float4(eta, 0.f, 0.f, 0.f);
+    t[0] = make_float4(Af[0], Af[1], Af[2], Af[3]);
+    t[1] = make_float4(Cf, eta, 0.f, 0.f);
 }
 
 // Float32 copies of the vertex coordinates, rounded to nearest (the x~_a of the filter).
@@ -80,19 +81,17 @@ __global__ void __launch_bounds__(256) vertex_bins_kernel(const double *__restri
     const bool act = p < d;
     const int pc = act ? p : d - 1;
     const float4 t0 = __ldg(reinterpret_cast<const float4 *>(tab + (int64_t)pc * 8));
-    const float eta = __ldg(tab + (int64_t)pc * 8 + 4);
-    const float Af[3] = {t0.x, t0.y, t0.z};
+    const float Cf = __ldg(tab + (int64_t)pc * 8 + 4), eta = __ldg(tab + (int64_t)pc * 8 + 5);
+    const float Af[4] = {t0.x, t0.y, t0.z, t0.w};
     for (int64_t v = (int64_t)blockIdx.x * vpb + threadIdx.x / Dt; v < nv; v += (int64_t)gridDim.x * vpb) {
-        float u = t0.w;
+        float u = Cf;
 #pragma unroll
         for (int a = N - 1; a >= 0; --a) u = __fmaf_rn(__ldg(xf + v * N + a), Af[a], u);
         const int tlo = __float_as_int(__fadd_ru(__fsub_rd(u, eta), kMagic));
         const int thi = __float_as_int(__fadd_ru(__fadd_ru(u, eta), kMagic));
         int b = clamp_bin(thi, 0, T);
         if (tlo != thi) {
-            double xd[3] = {0.0, 0.0, 0.0};
-            for (int a = 0; a < N; ++a) xd[a] = coords[v * N + a];
-            const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
+            const double h = heightv<N>(coords + v * N, dirs + (int64_t)pc * N);
             b = exact_bin_from(h, beta, T, b);
         }
         // every column gets a valid bin: a column past d (the last tile's padding) carries the
@@ -305,15 +304,15 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     const bool act = p < d;
     const int pc = act ? p : d - 1;
     const float4 t0 = __ldg(reinterpret_cast<const float4 *>(tab + (int64_t)pc * 8));
-    const float eta = __ldg(tab + (int64_t)pc * 8 + 4);
-    const float Af[3] = {t0.x, t0.y, t0.z};
+    const float Cf = __ldg(tab + (int64_t)pc * 8 + 4), eta = __ldg(tab + (int64_t)pc * 8 + 5);
+    const float Af[4] = {t0.x, t0.y, t0.z, t0.w};
     // CTA-uniform steps of nw * VG vertices (so that the periodic flush is a block-wide barrier),
     // at most P.flush_every steps between flushes
     const int64_t cstep = (int64_t)nw * VG;
     const int nvm1 = (int)(nv - 1);                  // vertex ids are int32
     const int64_t gstep = (int64_t)gridDim.x * cstep;
     // coordinates and weights of the warp's next group, loaded one step ahead
-    float xn[VG][3];
+    float xn[VG][N];
     int2 wn[VG];
     auto load_group = [&](int64_t base) {
         const int v0 = (int)(base + (int64_t)wid * VG);
@@ -329,7 +328,7 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     int since = 0;
     for (int64_t base = (int64_t)blockIdx.x * cstep; base < nv; base += gstep) {
         const int v0 = (int)(base + (int64_t)wid * VG);
-        float x[VG][3];
+        float x[VG][N];
         int2 w[VG];
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
         uint32_t pend = 0;
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
-            float u = t0.w;
+            float u = Cf;
 #pragma unroll
             for (int a = N - 1; a >= 0; --a) u = __fmaf_rn(x[g][a], Af[a], u);
             const int tlo = __float_as_int(__fadd_ru(__fsub_rd(u, eta), kMagic));
@@ -365,9 +364,7 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
                 const int g = __ffs(pend) - 1;
                 pend &= pend - 1;
                 const int v = min(v0 + g, nvm1);
-                double xd[3] = {0.0, 0.0, 0.0};
-                for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
-                const double h = height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)pc * N);
+                const double h = heightv<N>(coords + (int64_t)v * N, dirs + (int64_t)pc * N);
                 int bg = 0, wx = 0, wy = 0;
 #pragma unroll
                 for (int k = 0; k < VG; ++k)
@@ -624,13 +621,13 @@ __global__ void __launch_bounds__(256) range_lower_bound_kernel(const double *__
     __shared__ double sb[32];
     __shared__ float ss[32];
     const int v = (int)(uint32_t)(*key & 0xffffffffull);
-    double xd[3] = {0.0, 0.0, 0.0};
+    double xd[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
     double best = 0.0;
     float smax = 0.f;
     for (int p = threadIdx.x; p < d; p += blockDim.x) {
-        best = fmax(best, fabs(height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)p * N)));
+        best = fmax(best, fabs(heightv<N>(xd, dirs + (int64_t)p * N)));
         float s2 = 0.f;
 #pragma unroll
         for (int a = 0; a < N; ++a) {
@@ -713,7 +710,7 @@ __global__ void __launch_bounds__(256) max_abs_candidates_kernel(const double *_
         __syncthreads();
         for (int64_t ci = gw; ci < count; ci += nw) {
             const int v = cand[4 + ci];
-            float x[3] = {0.f, 0.f, 0.f};
+            float x[N];
 #pragma unroll
             for (int a = 0; a < N; ++a) x[a] = __ldg(xf + (int64_t)v * N + a);
             for (int j = lane; j < np; j += 32) {
@@ -725,9 +722,7 @@ __global__ void __launch_bounds__(256) max_abs_candidates_kernel(const double *_
                 }
                 const float E = __fmul_ru(mag, 0x1p-19f) + 0x1p-126f;
                 if (__fadd_ru(fabsf(h), E) >= L) {
-                    double xd[3] = {0.0, 0.0, 0.0};
-                    for (int a = 0; a < N; ++a) xd[a] = coords[(int64_t)v * N + a];
-                    const double hd = fabs(height3<N>(xd[0], xd[1], xd[2], dirs + (int64_t)(p0 + j) * N));
+                    const double hd = fabs(heightv<N>(coords + (int64_t)v * N, dirs + (int64_t)(p0 + j) * N));
                     atomicMax(Mbits, (unsigned long long)__double_as_longlong(hd));
                 }
             }
@@ -832,7 +827,8 @@ cudaError_t launch_dir_filters(int n, const double *dirs, int d, int T, const do
     const unsigned g = (unsigned)((d + 127) / 128);
     if (n == 1) dir_filter_kernel<1><<<g, 128, 0, st>>>(dirs, d, T, range, tab);
     else if (n == 2) dir_filter_kernel<2><<<g, 128, 0, st>>>(dirs, d, T, range, tab);
-    else dir_filter_kernel<3><<<g, 128, 0, st>>>(dirs, d, T, range, tab);
+    else if (n == 3) dir_filter_kernel<3><<<g, 128, 0, st>>>(dirs, d, T, range, tab);
+    else dir_filter_kernel<4><<<g, 128, 0, st>>>(dirs, d, T, range, tab);
     return cudaGetLastError();
 }
 
@@ -853,7 +849,8 @@ cudaError_t launch_vertex_bins(int n, const double *coords, const float *xf, int
 #define VB(NN) vertex_bins_kernel<NN><<<g, threads, 0, st>>>(coords, xf, nv, dirs, tab, d, dtile, Dt, T, beta, bins)
     if (n == 1) VB(1);
     else if (n == 2) VB(2);
-    else VB(3);
+    else if (n == 3) VB(3);
+    else VB(4);
 #undef VB
     return cudaGetLastError();
 }
@@ -872,9 +869,9 @@ cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, co
             vertex_scatter_kernel<NN, SS><<<grid, kSimplexThreads, sm, st>>>(a, coords, xf, nv, dirs, tab, beta, bins); \
     } while (0)
     if (nsplit == 1) {
-        if (n == 1) VS(1, 1); else if (n == 2) VS(2, 1); else VS(3, 1);
+        if (n == 1) VS(1, 1); else if (n == 2) VS(2, 1); else if (n == 3) VS(3, 1); else VS(4, 1);
     } else {
-        if (n == 1) VS(1, 2); else if (n == 2) VS(2, 2); else VS(3, 2);
+        if (n == 1) VS(1, 2); else if (n == 2) VS(2, 2); else if (n == 3) VS(3, 2); else VS(4, 2);
     }
 #undef VS
     if (e != cudaSuccess) return e;
@@ -898,7 +895,8 @@ static cudaError_t launch_simplex_fwd_s(const SimplexFwdArgs &a, int grid, cudaS
     case 1: SF(1); break;
     case 2: SF(2); break;
     case 3: SF(3); break;
-    default: SF(4); break;
+    case 4: SF(4); break;
+    default: SF(5); break;
     }
 #undef SF
     if (e != cudaSuccess) return e;
@@ -927,7 +925,8 @@ cudaError_t launch_chunk_local(const int32_t *simp, int64_t k, int m, uint16_t *
     switch (m) {
     case 2: chunk_local_kernel<2><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
     case 3: chunk_local_kernel<3><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
-    default: chunk_local_kernel<4><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
+    case 4: chunk_local_kernel<4><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
+    default: chunk_local_kernel<5><<<(unsigned)nch, 512, 0, st>>>(simp, k, local, cverts, cnu); break;
     }
     return cudaGetLastError();
 }
@@ -951,7 +950,8 @@ static cudaError_t launch_simplex_fwd_staged_s(const SimplexFwdArgs &a, int grid
     switch (a.m) {
     case 2: SS(2); break;
     case 3: SS(3); break;
-    default: SS(4); break;
+    case 4: SS(4); break;
+    default: SS(5); break;
     }
 #undef SS
     if (e != cudaSuccess) return e;
@@ -960,7 +960,7 @@ static cudaError_t launch_simplex_fwd_staged_s(const SimplexFwdArgs &a, int grid
 
 cudaError_t launch_simplex_fwd_staged(int nsplit, const SimplexFwdArgs &a, int grid, cudaStream_t st)
 {
-    if (a.Dt != 32 || a.m < 2 || a.m > 4 || !a.swp) return cudaErrorInvalidValue;
+    if (a.Dt != 32 || a.m < 2 || a.m > kMaxSimplexDim + 1 || !a.swp) return cudaErrorInvalidValue;
     return nsplit == 1 ? launch_simplex_fwd_staged_s<1>(a, grid, st) : launch_simplex_fwd_staged_s<2>(a, grid, st);
 }
 
@@ -981,7 +981,8 @@ cudaError_t launch_simplicial_max_abs(int n, const double *coords, const float *
     } while (0)
     if (n == 1) MA(1);
     else if (n == 2) MA(2);
-    else MA(3);
+    else if (n == 3) MA(3);
+    else MA(4);
 #undef MA
     return cudaGetLastError();
 }
@@ -994,7 +995,8 @@ cudaError_t launch_simplex_weights_max(const int32_t *simp, int64_t k, int m, co
     switch (m) {
     case 2: simplex_weights_max_kernel<2><<<g, 256, 0, st>>>(simp, k, vw, sw); break;
     case 3: simplex_weights_max_kernel<3><<<g, 256, 0, st>>>(simp, k, vw, sw); break;
-    default: simplex_weights_max_kernel<4><<<g, 256, 0, st>>>(simp, k, vw, sw); break;
+    case 4: simplex_weights_max_kernel<4><<<g, 256, 0, st>>>(simp, k, vw, sw); break;
+    default: simplex_weights_max_kernel<5><<<g, 256, 0, st>>>(simp, k, vw, sw); break;
     }
     return cudaGetLastError();
 }
@@ -1019,7 +1021,8 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
             case 0: simplex_bwd_kernel<1><<<g, 256, 0, st>>>(nullptr, k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
             case 1: simplex_bwd_kernel<2><<<g, 256, 0, st>>>(simp[1], k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
             case 2: simplex_bwd_kernel<3><<<g, 256, 0, st>>>(simp[2], k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
-            default: simplex_bwd_kernel<4><<<g, 256, 0, st>>>(simp[3], k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
+            case 3: simplex_bwd_kernel<4><<<g, 256, 0, st>>>(simp[3], k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
+            default: simplex_bwd_kernel<5><<<g, 256, 0, st>>>(simp[4], k, sign, vw, bins, Dt, dt, d, T, S, Iacc); break;
             }
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -1078,7 +1081,8 @@ cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k
     case 1: return launch_simplex_ecf_m<1>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
     case 2: return launch_simplex_ecf_m<2>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
     case 3: return launch_simplex_ecf_m<3>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
-    default: return launch_simplex_ecf_m<4>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    case 4: return launch_simplex_ecf_m<4>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
+    default: return launch_simplex_ecf_m<5>(h64, ghist, g, sm, simp, sw, k, sign, weighted, bins, T, out, nv, st);
     }
 }
 

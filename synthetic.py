@@ -242,6 +242,21 @@ def freudenthal_lists(dims) -> list:
     return lists
 
 
+def freudenthal_mesh(dims, seed: int, jitter: float = 0.2) -> Simplicial:
+    """The Freudenthal triangulation of a jittered full grid in R^n (any n): grid points at
+    -1 + 2 i / (L - 1) per axis, each moved by U(+-jitter cell), with all simplices of
+    freudenthal_lists(dims); u8 weights ~ U{0..255}."""
+    rng = np.random.default_rng(seed)
+    n = len(dims)
+    axes = [(-1.0 + 2.0 * np.arange(L, dtype=np.float64) / (L - 1)) if L > 1 else np.zeros(1) for L in dims]
+    mesh = np.meshgrid(*reversed(axes), indexing="ij")
+    X = np.stack([m.ravel() for m in reversed(mesh)], axis=1)
+    cell = np.array([2.0 / (L - 1) if L > 1 else 0.0 for L in dims])
+    X = X + rng.uniform(-jitter, jitter, X.shape) * cell
+    w = rng.integers(0, 256, size=X.shape[0], dtype=np.uint8)
+    return Simplicial(coords=np.ascontiguousarray(X), simplices=freudenthal_lists(dims), weights=w)
+
+
 def tetra_grid(side: int, seed: int, jitter: float = 0.2) -> Simplicial:
     """Solid side^3 jittered grid in [-1,1]^3 cut into tetrahedra (six per cube cell, one per
     ordering of the axes: the path lower corner -> +e_a -> +e_a+e_b -> upper corner), with all
