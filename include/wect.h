@@ -353,6 +353,20 @@ WECT_API wect_status wect_profile_read(double *kernel_ms, int64_t *launches);
  */
 WECT_API wect_status wect_debug_fail_alloc(int64_t k);
 
+/*
+ * Stencil-kernel selection for full cubical grids, a test and tuning hook.  The transform of a
+ * grid has two exact kernels that give identical integers: one adds each vertex's octant
+ * contribution to its bin, the other (one histogram plane only: u8, unweighted or narrow
+ * weights) walks the bin boundaries of each grid row and adds prefix-sum differences.
+ *   variant 0   choose by a cost estimate (default): the run kernel for long rows and few
+ *               thresholds per row
+ *   variant 1   the per-vertex kernel only
+ *   variant 2   the run kernel wherever it applies
+ * Process-wide; affects compute calls made afterwards (a batch's tuned shape takes precedence,
+ * and graphs already captured keep their kernel).  INVALID_ARG for another value.
+ */
+WECT_API wect_status wect_debug_stencil_variant(int variant);
+
 #ifdef __cplusplus
 }
 #endif

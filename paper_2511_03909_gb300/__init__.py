@@ -97,6 +97,7 @@ def _declare(L):
         "wect_cubical_compute_static": (_st, [_i, _p, _p, _i, _p, _i, _i, _d, _d, _p, _p]),
         "wect_cubical_static_status": (_st, [_p]),
         "wect_debug_fail_alloc": (_st, [_i64]),
+        "wect_debug_stencil_variant": (_st, [_i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -116,7 +117,7 @@ def exported_symbols():
         "wect_batch_autotune",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
         "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_cubical_static_status",
-        "wect_debug_fail_alloc",
+        "wect_debug_fail_alloc", "wect_debug_stencil_variant",
     ]
 
 
@@ -170,6 +171,12 @@ def debug_fail_alloc(k: int):
     """Test hook: the next k device allocations of the library succeed and the one after fails
     as out of memory (k < 0 disarms)."""
     _check(load().wect_debug_fail_alloc(int(k)))
+
+
+def stencil_variant(variant: int):
+    """wect_debug_stencil_variant: 0 = choose the cubical stencil kernel by cost, 1 = the
+    per-vertex kernel only, 2 = the run-based kernel wherever it applies."""
+    _check(load().wect_debug_stencil_variant(int(variant)))
 
 
 def version() -> str:

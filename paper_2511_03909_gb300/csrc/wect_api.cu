@@ -260,6 +260,7 @@ struct GraphEntry {
 
 struct BatchConfig {
     int dpl = 0, Dt = 0;
+    bool run = false;             // the run-based kernel (dpl 1)
 };
 
 struct wect_batch_s {
@@ -272,6 +273,7 @@ struct wect_batch_s {
     int kflush = 1 << 16;
     int64_t total_nv = 0;
     int maxL0 = 1;
+    double meanL0 = 1.0;           // mean row length over all rows of the batch
     std::vector<GridDesc> h_grids;
     std::vector<int64_t> v_off;
     GridDesc *d_grids = nullptr;
@@ -338,15 +340,65 @@ struct CubShape {
     int dpl, Dt, ctas_per_sm, grid;
     size_t smem;
     bool gh = false;              // global-histogram variant (T x Dt does not fit shared memory)
+    bool run = false;             // run-based kernel (walks bin boundaries along the rows)
 };
+
+// Stencil variant selection: 0 = by cost estimate, 1 = per-vertex kernel only, 2 = the run-based
+// kernel wherever it applies (test hook wect_debug_stencil_variant).
+static std::atomic<int> g_stencil_variant{0};
+
+// Should a grid with rows of L0 vertices (mean) take the run-based kernel for T thresholds over a
+// range of width span (NaN: the default range)?  A row of a spread-out direction set crosses
+// about 2 E|s_0| / step ~ 1.2 / step bin boundaries; a boundary costs ~14 instructions and a row
+// ~60 more, against ~9 per vertex in the per-vertex kernel (measured instruction counts).
+static bool run_profitable(int n, double meanL0, int T, double span)
+{
+    if (!(span > 0.0)) span = 2.0 * std::sqrt((double)n);
+    const double step = span / (double)(T - 1);
+    const double runs = 1.0 + 1.2 / step;
+    return 14.0 * runs + 60.0 < 0.85 * 8.8 * meanL0;
+}
+
+// Run-based kernel shape: one direction per lane, the widest tile up to 256 that fits.
+static bool run_shape(int n, int d, int T, int maxL0, CubShape &out, int Dt_req = 0)
+{
+    const size_t limit = smem_optin() - 1024;
+    int Dmax = 32;
+    while (Dmax < d && Dmax < 256) Dmax *= 2;
+    for (int Dt = (Dt_req > 0 ? Dt_req : Dmax); Dt >= 32; Dt /= 2) {
+        const size_t sm = cubical_run_smem(n, T, Dt, maxL0);
+        if (sm > limit) {
+            if (Dt_req > 0) return false;
+            continue;
+        }
+        out.dpl = 1;
+        out.Dt = Dt;
+        out.smem = sm;
+        out.ctas_per_sm = std::max(1, std::min((int)(smem_per_sm() / (sm + 2048)), 2048 / cubical_run_threads()));
+        out.grid = sm_count() * out.ctas_per_sm;
+        out.gh = false;
+        out.run = true;
+        return true;
+    }
+    return false;
+}
 
 // Tile shape of the stencil kernel: the widest direction tile (fewest passes over the grid)
 // that fits shared memory, then the most directions per lane.  dpl_req / Dt_req pin a shape.
-static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0)
+// With run_ok (one histogram plane) the run-based kernel is taken when it is estimated cheaper
+// (meanL0 rows, a threshold range of width span), or always under the test hook.
+static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0,
+                      double meanL0 = 0.0, double span = 0.0)
 {
     const int threads = cubical_fwd_threads();
     const int warps = threads / 32;
     const size_t limit = smem_optin() - 1024;
+    out.run = false;
+    if (nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1) {
+        const bool want = g_stencil_variant.load() == 2 ||
+                          run_profitable(n, meanL0 > 0.0 ? meanL0 : (double)maxL0, T, span);
+        if (want && run_shape(n, d, T, maxL0, out)) return true;
+    }
     int Dmax = 32;
     while (Dmax < d && Dmax < 32 * 4 * warps) Dmax *= 2;
     for (int Dt = (Dt_req > 0 ? Dt_req : Dmax); Dt >= 32; Dt /= 2) {
@@ -446,7 +498,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     }
     KL(launch_fwd_prep(L.n, dirs, d, T, lo, hi, dflt ? 1 : 0, ws.M.p, ws.range.p, ws.beta.p, ws.perm.p, ws.octb.p,
                        ws.counter.p, L.status, direct ? nullptr : reinterpret_cast<unsigned long long *>(out),
-                       out_rows * T, st),
+                       out_rows * T, st, sh.run ? 1 : 0),
        "fwd_prep");
     CubicalFwdArgs a{};
     a.grids = L.d_grids;
@@ -459,7 +511,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.range = ws.range.p;
     a.beta = ws.beta.p;
     a.Dt = sh.Dt;
-    a.CP = cubical_fwd_pitch(L.maxL0);
+    a.CP = sh.run ? cubical_run_pitch(L.maxL0) : cubical_fwd_pitch(L.maxL0);
     a.perm = ws.perm.p;
     a.kflush = L.kflush;
     a.climit = L.climit;
@@ -469,11 +521,15 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cs);
+        auto launch = [&]() {
+            return sh.run ? launch_cubical_run(L.n, a, grid, sh.smem, st)
+                          : launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st);
+        };
         if (cs == cudaStreamCaptureStatusNone) {
             ProfScope prof(st);
-            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st), "cubical_fwd");
+            KL(launch(), "cubical_fwd");
         } else {
-            KL(launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st), "cubical_fwd");
+            KL(launch(), "cubical_fwd");
         }
     }
     if (!direct) KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), out_rows, T, st), "scan_rows");
@@ -858,14 +914,14 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
                                    cudaStream_t st)
 {
     CubShape sh;
-    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh))
+    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh, 0, 0, (double)c->L[0], hi - lo))
         return fail(WECT_ERR_UNSUPPORTED, "grid rows of %d vertices do not fit the kernel's shared row buffers", c->L[0]);
     if (c->L[0] > c->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
     wect_status s = ensure_common_ws(c->ws, T, d);
     if (s) return s;
     const int rows = c->L[1] * c->L[2];
     const bool direct = false;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), sh.grid);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1), sh.grid);
     if (c->ws.items_key != key) {
         std::vector<GridDesc> gv(1);
         gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
@@ -1178,6 +1234,9 @@ static wect_status batch_finish(wect_batch b, cudaStream_t st)
         b->maxL0 = std::max(b->maxL0, b->h_grids[i].L[0]);
     }
     b->total_nv = off;
+    int64_t rows = 0;
+    for (auto &g : b->h_grids) rows += g.rows;
+    b->meanL0 = (double)off / (double)std::max<int64_t>(rows, 1);
     CK(dev_malloc((void **)&b->d_grids, b->h_grids.size() * sizeof(GridDesc)), "alloc grids");
     CK(cudaMemcpy(b->d_grids, b->h_grids.data(), b->h_grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice), "upload grids");
     CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
@@ -1331,12 +1390,18 @@ extern "C" wect_status wect_batch_set_weights(wect_batch b, const void *w, wect_
 extern "C" int wect_batch_count(wect_batch b) { return b ? b->count : 0; }
 extern "C" int64_t wect_batch_total_vertices(wect_batch b) { return b ? b->total_nv : 0; }
 
-static bool batch_shape(wect_batch b, int d, int T, CubShape &sh)
+static bool batch_shape(wect_batch b, int d, int T, double span, CubShape &sh)
 {
     auto it = b->tuned.find({d, T});
-    if (it != b->tuned.end()) return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt);
-    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh);
+    if (it != b->tuned.end()) {
+        if (it->second.run) return b->nsplit == 1 && run_shape(b->n, d, T, b->maxL0, sh, it->second.Dt);
+        return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt);
+    }
+    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span);
 }
+
+// Tile-shape code for cache keys: dpl, negative for the global-histogram variant, 100 for runs.
+static int shape_code(const CubShape &sh) { return sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1); }
 
 // Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
 // directly) when every complex fits one flush; otherwise row chunks balanced over the grid.
@@ -1346,7 +1411,7 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
     for (auto &g : b->h_grids) maxnv = std::max<int64_t>(maxnv, g.nv);
     const int ntiles = (d + sh.Dt - 1) / sh.Dt;
     direct = !sh.gh && maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), direct ? 1 : 0);
+    auto key = std::make_tuple(d, T, sh.Dt, shape_code(sh), direct ? 1 : 0);
     if (b->ws.items_key == key) return WECT_OK;
     std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, T, b->kflush, 4 * sh.grid, direct);
     wect_status s = upload_items(b->ws, items, st);
@@ -1374,12 +1439,13 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
-    if (!batch_shape(b, d, T, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape of the stencil kernel fits (T = %d)", T);
+    if (!batch_shape(b, d, T, hi - lo, sh))
+        return fail(WECT_ERR_UNSUPPORTED, "no tile shape of the stencil kernel fits (T = %d)", T);
     if (b->maxL0 > b->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     bool direct = false;
     if ((s = batch_items(b, d, T, sh, direct, st))) return s;
-    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, sh.dpl * (sh.gh ? -1 : 1));
+    auto key = std::make_tuple((const void *)dirs, d, T, lo, hi, (void *)out, (void *)st, sh.Dt, shape_code(sh));
     auto it = b->graphs.find(key);
     if (it != b->graphs.end() && it->second.deps != graph_deps(b->ws)) {
         CK(cudaStreamSynchronize(st), "sync");          // a replay of it may still be running
@@ -1390,7 +1456,8 @@ extern "C" wect_status wect_batch_compute(wect_batch b, const double *dirs, int 
     }
     if (it == b->graphs.end()) {
         // capture the launch sequence once on a private stream, replay it on the caller's stream
-        CK(prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, sh.smem), "prepare");
+        CK(sh.run ? prepare_cubical_run(b->n, sh.smem) : prepare_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, sh.smem),
+           "prepare");
         CK(cudaStreamSynchronize(st), "sync");
         GraphEntry ge;
         const int64_t before = g_launches.load();
@@ -1428,12 +1495,12 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
     CubShape sh;
-    if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+    if (!batch_shape(b, d, T, hi - lo, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
     if (b->maxL0 > b->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows too long");
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     // one item list per complex, concatenated; each complex launched on its own
     std::vector<int> &starts = b->loop_starts;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.dpl * (sh.gh ? -1 : 1), 7);
+    auto key = std::make_tuple(d, T, sh.Dt, shape_code(sh), 7);
     if (b->ws.items_key != key) {
         std::vector<WorkItem> all;
         starts.assign(b->count + 1, 0);
@@ -1448,8 +1515,10 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         if ((s = upload_items(b->ws, all, st))) return s;
         b->ws.items_key = key;
     }
-    KL(launch_setup_range_beta(lo, hi, 0, b->ws.M.p, T, b->ws.range.p, b->ws.beta.p, st), "setup_range_beta");
-    KL(launch_octant_sort(b->n, dirs, d, b->ws.perm.p, b->ws.octb.p, st), "octant_sort");
+    // range, beta and the direction order of the shape (octant groups, or |s_0| for the runs)
+    KL(launch_fwd_prep(b->n, dirs, d, T, lo, hi, 0, b->ws.M.p, b->ws.range.p, b->ws.beta.p, b->ws.perm.p,
+                       b->ws.octb.p, b->ws.counter.p, b->d_status, nullptr, 0, st, sh.run ? 1 : 0),
+       "fwd_prep");
     CK(cudaMemsetAsync(out, 0, (size_t)b->count * d * T * sizeof(int64_t), st), "memset");
     for (int i = 0; i < b->count; ++i) {
         CK(cudaMemsetAsync(b->ws.counter.p, 0, sizeof(int), st), "memset");
@@ -1464,13 +1533,15 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.range = b->ws.range.p;
         a.beta = b->ws.beta.p;
         a.Dt = sh.Dt;
-        a.CP = cubical_fwd_pitch(b->maxL0);
+        a.CP = sh.run ? cubical_run_pitch(b->maxL0) : cubical_fwd_pitch(b->maxL0);
         a.perm = b->ws.perm.p;
         a.kflush = b->kflush;
         a.climit = b->climit;
         a.direct = 0;
         a.out = reinterpret_cast<unsigned long long *>(out);
-        KL(launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, std::max(1, std::min(sh.grid, a.n_items)), sh.smem, st),
+        const int grid = std::max(1, std::min(sh.grid, a.n_items));
+        KL(sh.run ? launch_cubical_run(b->n, a, grid, sh.smem, st)
+                  : launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st),
            "fwd");
         KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out) + (int64_t)i * d * T, d, T, st), "scan");
     }
@@ -1535,18 +1606,25 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     std::lock_guard<std::mutex> lk(b->mu);
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     const int warps = cubical_fwd_threads() / 32;
-    std::vector<std::pair<int, int>> cands;
+    // candidates: (directions per lane, tile width, run-based kernel)
+    std::vector<std::tuple<int, int, bool>> cands;
     for (int dpl : {1, 2, 4})
-        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2) cands.push_back({dpl, Dt});
+        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2) cands.push_back({dpl, Dt, false});
+    if (b->nsplit == 1)
+        for (int Dt = 32; Dt <= 256; Dt *= 2) cands.push_back({1, Dt, true});
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    BatchConfig bc{0, 0};
-    for (auto [dpl, Dt] : cands) {
+    BatchConfig bc{0, 0, false};
+    for (auto [dpl, Dt, run] : cands) {
         if (Dt > 2 * std::max(d, 32 * dpl)) continue;
         CubShape sh;
-        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt) || sh.Dt != Dt || sh.dpl != dpl) continue;
+        if (run) {
+            if (!run_shape(b->n, d, T, b->maxL0, sh, Dt)) continue;
+        } else if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt) || sh.Dt != Dt || sh.dpl != dpl) {
+            continue;
+        }
         bool direct = false;
         if ((s = batch_items(b, d, T, sh, direct, st))) break;
         float ms_best = 1e30f;
@@ -1562,7 +1640,7 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
         if (s) break;
         if (ms_best < best) {
             best = ms_best;
-            bc = BatchConfig{dpl, Dt};
+            bc = BatchConfig{dpl, Dt, run};
         }
     }
     cudaEventDestroy(e0);
@@ -1581,6 +1659,13 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     }
     b->graphs.clear();
     b->ws.items_key = std::make_tuple(-1, -1, -1, -1, -1);
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_debug_stencil_variant(int variant)
+{
+    if (variant < 0 || variant > 2) return fail(WECT_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    g_stencil_variant.store(variant);
     return WECT_OK;
 }
 

@@ -76,9 +76,17 @@ __global__ void octant_sort_kernel(int n, const double *dirs, int d, int *perm, 
 // directions for non-finite values (status flag), resolves the range and fills beta, groups the
 // directions by octant and clears the work-queue head; every block clears the output table
 // (when given) with 16-byte stores.
+// Key of a direction in the run order: |s_0| (a non-finite component sorts last; the direction is
+// flagged as invalid anyway).
+__device__ __forceinline__ double run_key(const double *dirs, int n, int p)
+{
+    const double x = dirs[(int64_t)p * n];
+    return isfinite(x) ? fabs(x) : __longlong_as_double(0x7ff0000000000000ll);
+}
+
 __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                                 const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
-                                int *counter, int *status, unsigned long long *out, int64_t out_elems)
+                                int *counter, int *status, unsigned long long *out, int64_t out_elems, int run_order)
 {
     if (blockIdx.x == 0) {
         __shared__ int cnt[8], start[9], fill[8];
@@ -86,8 +94,21 @@ __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double 
             for (int i = threadIdx.x; i < d * n; i += blockDim.x)
                 if (!isfinite(dirs[i])) atomicOr(status, kStatusBadIndex);
         range_beta(lo, hi, use_default, Mbits, T, range, beta, threadIdx.x, blockDim.x);
-        octant_sort_block(n, dirs, d, perm, octb, cnt, start, fill);
+        if (!run_order) octant_sort_block(n, dirs, d, perm, octb, cnt, start, fill);
         if (threadIdx.x == 0) *counter = 0;
+    }
+    if (run_order) {
+        // directions in increasing |s_0| (ties by index: a total order, so perm is a permutation):
+        // the run kernel's lanes then walk similar numbers of bin boundaries per row
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < d; p += gridDim.x * blockDim.x) {
+            const double kp = run_key(dirs, n, p);
+            int r = 0;
+            for (int q = 0; q < d; ++q) {
+                const double kq = run_key(dirs, n, q);
+                r += (kq < kp || (kq == kp && q < p)) ? 1 : 0;
+            }
+            perm[r] = p;
+        }
     }
     if (out && out_elems > 0) {
         // an 8-byte aligned table: one scalar head element when it is not 16-byte aligned
@@ -343,13 +364,15 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
 
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
-                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st)
+                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
+                            int run_order)
 {
     if (out && (reinterpret_cast<uintptr_t>(out) & 7u)) return cudaErrorMisalignedAddress;   // int64 alignment
-    const int64_t work = out ? (out_elems / 2 + 255) / 256 : 1;
+    int64_t work = out ? (out_elems / 2 + 255) / 256 : 1;
+    if (run_order) work = std::max<int64_t>(work, (d + 255) / 256);
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, 152 * 4));
     fwd_prep_kernel<<<g, 256, 0, st>>>(n, dirs, d, T, lo, hi, use_default, Mbits, range, beta, perm, octb, counter,
-                                       status, out, out_elems);
+                                       status, out, out_elems, run_order);
     return cudaGetLastError();
 }
 

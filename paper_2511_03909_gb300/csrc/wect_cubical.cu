@@ -21,156 +21,13 @@
 // T x Dt int32 entries no longer fit shared memory (large T), the GH variant scatters every
 // update straight into the int64 difference table in global memory instead (same bins, same
 // integer sums; slower, but any T).
+#include "wect_cubical_common.cuh"
 #include "wect_device.cuh"
 #include "wect_launch.h"
 
 namespace wect {
 
 constexpr int kFwdThreads = 512;
-
-// ------------------------------------------------------------------ octant contributions
-
-// c_o(v) for every octant o from the int32 fixed-point weights of v's 3^n neighbourhood (the
-// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set).
-template <int N>
-__device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i1, int i2, int32_t *c /* [1 << N] */)
-{
-    constexpr int NOCT = 1 << N;
-    constexpr int NY = (N >= 2) ? 3 : 1;
-    constexpr int NZ = (N >= 3) ? 3 : 1;
-    const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
-    const bool ok0[3] = {i0 > 0, true, i0 < L0 - 1};
-    const bool ok1[3] = {i1 > 0, true, i1 < L1 - 1};
-    const bool ok2[3] = {i2 > 0, true, i2 < L2 - 1};
-    const int64_t v = (int64_t)i0 + (int64_t)L0 * ((int64_t)i1 + (int64_t)L1 * i2);
-    // box maxima over the 3^n neighbourhood, axis by axis: A[z][y][x] = max over the box spanning
-    // v and v + (x-1, y-1, z-1)
-    int32_t A[NZ][NY][3];
-#pragma unroll
-    for (int z = 0; z < NZ; ++z)
-#pragma unroll
-        for (int y = 0; y < NY; ++y) {
-            int32_t w[3];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                const int dy = (N >= 2) ? y - 1 : 0, dz = (N >= 3) ? z - 1 : 0;
-                const bool ok = ok0[x] && (N < 2 || ok1[y]) && (N < 3 || ok2[z]);
-                w[x] = ok ? __ldg(g.w + v + (x - 1) + (int64_t)L0 * (dy + (int64_t)L1 * dz)) : 0;
-            }
-            A[z][y][0] = max(w[0], w[1]);
-            A[z][y][1] = w[1];
-            A[z][y][2] = max(w[1], w[2]);
-        }
-    if (N >= 2) {
-#pragma unroll
-        for (int z = 0; z < NZ; ++z)
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                const int32_t a0 = A[z][0][x], a1 = A[z][NY > 1 ? 1 : 0][x], a2 = A[z][NY > 2 ? 2 : 0][x];
-                A[z][0][x] = max(a0, a1);
-                if (NY > 2) A[z][2][x] = max(a1, a2);
-            }
-    }
-    if (N >= 3) {
-#pragma unroll
-        for (int y = 0; y < NY; ++y)
-#pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                const int32_t a0 = A[0][y][x], a1 = A[NZ > 1 ? 1 : 0][y][x], a2 = A[NZ > 2 ? 2 : 0][y][x];
-                A[0][y][x] = max(a0, a1);
-                if (NZ > 2) A[2][y][x] = max(a1, a2);
-            }
-    }
-#pragma unroll
-    for (int o = 0; o < NOCT; ++o) {
-        int32_t acc = 0;
-#pragma unroll
-        for (int e = 0; e < NOCT; ++e) {
-            int idx[3] = {1, 1, 1};
-            bool ok = true;
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                if ((e >> a) & 1) {
-                    const bool up = (o >> a) & 1;            // sign corner is the upper end: the cell reaches back
-                    idx[a] = up ? 0 : 2;
-                    ok = ok && (a == 0 ? ok0[idx[a]] : (a == 1 ? ok1[idx[a]] : ok2[idx[a]]));
-                }
-            }
-            const int32_t wb = A[N >= 3 ? idx[2] : 0][N >= 2 ? idx[1] : 0][idx[0]];
-            if (ok) acc += (__popc(e) & 1) ? -wb : wb;
-        }
-        c[o] = acc;
-    }
-}
-
-// ------------------------------------------------------------------ forward helpers
-
-// Add the CTA's partial histograms into the int64 output block [d][T] and clear them.
-template <int NSPLIT>
-__device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int dtile, int d, const int *perm,
-                                              unsigned long long *out)
-{
-    const int hw = T * Dt;
-    if (blockDim.x % Dt == 0) {
-        // each thread keeps one column: no division and one perm load per thread
-        const int col = threadIdx.x % Dt, bstep = blockDim.x / Dt;
-        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
-        unsigned long long *orow = out + (int64_t)min(p, d - 1) * T;
-        for (int b = threadIdx.x / Dt; b < T; b += bstep) {
-            const int idx = b * Dt + col;
-            int64_t v;
-            if (NSPLIT == 1) {
-                v = hist[idx];
-            } else {
-                v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
-                hist[hw + idx] = 0;
-            }
-            hist[idx] = 0;
-            if (p < d && v != 0) atomicAdd(orow + b, (unsigned long long)v);
-        }
-        return;
-    }
-    for (int idx = threadIdx.x; idx < hw; idx += blockDim.x) {
-        const int b = idx / Dt, col = idx - b * Dt;
-        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
-        int64_t v;
-        if (NSPLIT == 1) {
-            v = hist[idx];
-        } else {
-            v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
-            hist[hw + idx] = 0;
-        }
-        hist[idx] = 0;
-        if (p < d && v != 0) atomicAdd(out + (int64_t)p * T + b, (unsigned long long)v);
-    }
-}
-
-// The item covered every row of its complex: the histogram is the complete difference table of
-// its directions.  Scan it over the thresholds (Algorithm 1's cumulative sum) and store the
-// transform directly (no atomics, no separate scan).
-template <int NSPLIT>
-__device__ __forceinline__ void cubical_flush_direct(int32_t *hist, int T, int Dt, int dtile, int d, const int *perm,
-                                                     unsigned long long *out)
-{
-    const int hw = T * Dt;
-    for (int col = threadIdx.x; col < Dt; col += blockDim.x) {
-        const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
-        long long acc = 0;
-        for (int q = 0; q < T; ++q) {
-            const int idx = q * Dt + col;
-            int64_t v;
-            if (NSPLIT == 1) {
-                v = hist[idx];
-            } else {
-                v = ((int64_t)hist[hw + idx] << 16) + (int64_t)(uint32_t)hist[idx];
-                hist[hw + idx] = 0;
-            }
-            hist[idx] = 0;
-            acc += v;
-            if (p < d) out[(int64_t)p * T + q] = (unsigned long long)acc;
-        }
-    }
-}
 
 // The float32 filter could not decide the bin of vertex (i0,i1,i2) in direction p: evaluate the
 // float64 height, find its exact bin and move the contribution if the tentative bin was wrong.
@@ -392,16 +249,6 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
 }
 
 // ------------------------------------------------------------------ forward
-
-// Barrier of the WC warps of one row group (warp-synchronous when the group is one warp).
-__device__ __forceinline__ void group_sync(int rgroup, int WC)
-{
-    if (WC == 1) {
-        __syncwarp();
-    } else {
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + rgroup), "r"(WC * 32) : "memory");
-    }
-}
 
 template <int N, int NSPLIT, int DPL, bool GH>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)

@@ -278,6 +278,13 @@ __device__ __forceinline__ void lds_v2u64(uint32_t addr, unsigned long long &a, 
     asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
 }
 
+__device__ __forceinline__ int lds_s32(uint32_t addr)
+{
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ long long lds_s64(uint32_t addr)
 {
     long long v;

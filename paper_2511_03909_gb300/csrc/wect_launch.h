@@ -96,6 +96,13 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bo
 int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();
 // The adjoint's octant sums for one direction chunk, then (once every chunk is summed) the routing.
+// The run-based stencil kernel (one int32 histogram plane; directions in the run order of
+// launch_fwd_prep; CP = cubical_run_pitch): same arguments and items as launch_cubical_fwd.
+cudaError_t launch_cubical_run(int n, const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t prepare_cubical_run(int n, size_t smem);
+int cubical_run_pitch(int maxL0);
+size_t cubical_run_smem(int n, int T, int Dt, int maxL0);
+int cubical_run_threads();
 cudaError_t launch_cubical_bwd_rsum(int n, const CubicalBwdArgs &a, int n_items, size_t smem_rsum, cudaStream_t st);
 cudaError_t launch_cubical_bwd_route(int n, const CubicalBwdArgs &a, cudaStream_t st);
 size_t cubical_bwd_rsum_smem(int n, int d, int T, int R);
@@ -155,9 +162,12 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
 cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st);
 // Fused preparation of the cubical forward: direction check (status may be null), range and beta,
 // octant grouping, work-queue head, and (out non-null) a cleared output table of out_elems int64.
+// run_order: perm lists the directions by increasing |s_0| (the run kernel's order) instead of
+// grouped by octant (octb is then not written).
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
-                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st);
+                            int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
+                            int run_order = 0);
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
 cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
                                cudaStream_t st);
