@@ -204,19 +204,33 @@ def cells_of(dims):
 # ------------------------------------------------------------------ traffic from the committed profile
 
 
-def _traffic_per_launch():
-    """DRAM bytes per launch of the forward kernel from the committed ncu summary, or None when
-    the kernel source changed since the counters were taken."""
+# The committed ncu summary of each stencil kernel on the 128^3 workload, and the sources the
+# kernel is compiled from (the counters are stale once any of them changed).
+_PROFILES = {
+    "cubical_fwd_kernel": ("cubical_fwd_voxel3d_128.md", ("wect_cubical.cu", "wect_cubical_common.cuh",
+                                                          "wect_device.cuh")),
+    "cubical_run_kernel": ("cubical_run_voxel3d_128.md", ("wect_cubical_run.cu", "wect_cubical_common.cuh",
+                                                          "wect_device.cuh")),
+}
+
+
+def _sources_sha(names):
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_2511_03909_gb300", "csrc")
-    prof = os.path.join(ROOT, "profiles", "cubical_fwd_voxel3d_128.md")
+    hs = hashlib.sha256()
+    for name in names:
+        hs.update(open(os.path.join(csrc, name), "rb").read())
+    return hs.hexdigest()[:16]
+
+
+def _traffic_per_launch(kernel):
+    """DRAM bytes per launch of the kernel from its committed ncu summary, or None when the
+    kernel's sources changed since the counters were taken."""
     try:
-        hs = hashlib.sha256()
-        for name in ("wect_cubical.cu", "wect_device.cuh"):     # the forward kernel's sources
-            hs.update(open(os.path.join(csrc, name), "rb").read())
-        h = hs.hexdigest()[:16]
-        for ln in open(prof):
+        prof, names = _PROFILES[kernel]
+        h = _sources_sha(names)
+        for ln in open(os.path.join(ROOT, "profiles", prof)):
             if ln.startswith("traffic_bytes_per_launch:"):
                 _, val, _, sha = ln.split()
                 return float(val) if sha == h else None
@@ -371,23 +385,35 @@ def run_gpu(args):
         return 0
 
     peaks, src = _peaks()
-    # roofline of the dominant kernel (the fused stencil scatter): issue-bound arithmetic.
-    # Algorithmic work per vertex.direction update: 3 lane operations (the height fma, the
-    # rounding to a bin, the integer add into the histogram); peak lane-op rate = 152 SMs x 128
-    # lanes x the SM clock.
+    # roofline of the dominant kernel (the stencil kernel of the transform).  Unit of work: one
+    # vertex.direction update of the method (the height fma, the rounding to a bin, the integer
+    # add into the histogram: 3 lane operations); peak lane-op rate = 152 SMs x 128 lanes x the SM
+    # clock.  The run-based kernel reaches the same sums with fewer operations on long rows (one
+    # update per bin boundary), so against this roof it is a throughput ratio.  Floors of the
+    # unit of work: HBM (inputs read once, table written once), the lane-op roof, and the shared
+    # atomic pipe (one 32-bit red.shared per update at ~25 per clock per SM, measured with a
+    # probe kernel on this GPU).
+    kernel = P.last_stencil_kernel()
     nv = int(np.prod(wl.dims))
     kernel_ms = kern_ms / max(kern_n, 1)
-    ops = 3.0 * nv * d
+    units = nv * d
+    ops = 3.0 * units
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_ops = 152 * 128 * sm_mhz * 1e6
     achieved = ops / (kernel_ms / 1e3)
     hbm_bytes = nv * 1 + d * T * 8 + d * 3 * 8
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    floors = {"hbm_us": hbm_bytes / (hbm_peak * 1e9) * 1e6, "alu_us": ops / peak_ops * 1e6,
+              "smem_atomic_us": units / (25.0 * 152 * sm_mhz * 1e6) * 1e6}
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak_ops, "traffic": _traffic_per_launch(),
-            "kernel": "cubical_fwd_kernel", "kernel_ms": kernel_ms,
+            "frac": achieved / peak_ops, "traffic": _traffic_per_launch(kernel),
+            "kernel": kernel, "kernel_ms": kernel_ms, "units_per_launch": units,
+            "unit_of_work": "vertex.direction update, 3 lane ops",
             "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({src} sm_max_mhz)",
+            "floors_us": floors, "floor_us": max(floors.values()),
+            "frac_of_floor": max(floors.values()) / (kernel_ms * 1e3),
             "hbm_gbs": hbm_bytes / (kernel_ms / 1e3) / 1e9,
-            "hbm_frac": hbm_bytes / (kernel_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+            "hbm_frac": hbm_bytes / (kernel_ms / 1e3) / 1e9 / hbm_peak}
 
     # CPU baseline: the oracle on a bounded sample (a few directions) of the same workload
     cpu = None

@@ -328,6 +328,12 @@ WECT_API const char *wect_last_error(void);
 WECT_API const char *wect_version(void);
 
 /*
+ * Name of the stencil kernel that the last cubical forward enqueued by this process used
+ * ("cubical_fwd_kernel", "cubical_run_kernel", ...; "" before the first), for benchmark reports.
+ */
+WECT_API const char *wect_last_stencil_kernel(void);
+
+/*
  * Number of kernels this library launched (or replayed inside its graphs) on the calling
  * process since load, for launch accounting.
  */

@@ -91,6 +91,7 @@ def _declare(L):
         "wect_batch_destroy": (None, [_p]),
         "wect_last_error": (C.c_char_p, []),
         "wect_version": (C.c_char_p, []),
+        "wect_last_stencil_kernel": (C.c_char_p, []),
         "wect_kernel_launch_count": (_i64, []),
         "wect_profile_enable": (_st, [_i]),
         "wect_profile_read": (_st, [_p, _p]),
@@ -115,7 +116,7 @@ def exported_symbols():
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
         "wect_batch_autotune",
-        "wect_batch_destroy", "wect_last_error", "wect_version", "wect_kernel_launch_count",
+        "wect_batch_destroy", "wect_last_error", "wect_version", "wect_last_stencil_kernel", "wect_kernel_launch_count",
         "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_cubical_static_status",
         "wect_debug_fail_alloc", "wect_debug_stencil_variant",
     ]
@@ -165,6 +166,11 @@ def profile_read():
     n = C.c_int64()
     _check(load().wect_profile_read(C.byref(ms), C.byref(n)))
     return float(ms.value), int(n.value)
+
+
+def last_stencil_kernel() -> str:
+    """Name of the stencil kernel the last cubical forward used."""
+    return load().wect_last_stencil_kernel().decode()
 
 
 def debug_fail_alloc(k: int):

@@ -21,6 +21,7 @@ using namespace wect;
 // ------------------------------------------------------------------ errors and accounting
 
 static thread_local std::string g_last_error;
+static std::atomic<int> g_last_stencil{0};      // 0 none, 1 per-vertex, 2 run-based, 3 global histogram
 static std::atomic<int64_t> g_launches{0};
 
 static wect_status fail(wect_status st, const char *fmt, ...)
@@ -349,14 +350,17 @@ static std::atomic<int> g_stencil_variant{0};
 
 // Should a grid with rows of L0 vertices (mean) take the run-based kernel for T thresholds over a
 // range of width span (NaN: the default range)?  A row of a spread-out direction set crosses
-// about 2 E|s_0| / step ~ 1.2 / step bin boundaries; a boundary costs ~14 instructions and a row
-// ~60 more, against ~9 per vertex in the per-vertex kernel (measured instruction counts).
+// about 2 E|s_0| / step ~ 1.2 / step bin boundaries.  Measured on the 128^3 u8 volume with 256
+// Fibonacci directions (CUDA events, the library's kernel hook): the run kernel costs ~140 us of
+// row set-up (octant contributions, prefix sums, end bins; latency-bound) plus ~4 us per million
+// boundaries, the per-vertex kernel 200-270 us whatever T.  So the runs win only with a few
+// boundaries per long row: T = 8 took 178 us against 267 us, T = 32 286 us against 216 us.
 static bool run_profitable(int n, double meanL0, int T, double span)
 {
     if (!(span > 0.0)) span = 2.0 * std::sqrt((double)n);
     const double step = span / (double)(T - 1);
     const double runs = 1.0 + 1.2 / step;
-    return 14.0 * runs + 60.0 < 0.85 * 8.8 * meanL0;
+    return runs <= 4.0 && meanL0 >= 96.0;
 }
 
 // Run-based kernel shape: one direction per lane, the widest tile up to 256 that fits.
@@ -521,6 +525,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cs);
+        g_last_stencil.store(sh.run ? 2 : (sh.gh ? 3 : 1));
         auto launch = [&]() {
             return sh.run ? launch_cubical_run(L.n, a, grid, sh.smem, st)
                           : launch_cubical_fwd(L.n, L.nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st);
@@ -1689,7 +1694,17 @@ extern "C" void wect_batch_destroy(wect_batch b)
 // ------------------------------------------------------------------ misc
 
 extern "C" const char *wect_last_error(void) { return g_last_error.c_str(); }
-extern "C" const char *wect_version(void) { return "wect-gb300 0.1 (sm_103a)"; }
+extern "C" const char *wect_version(void) { return "wect-gb300 0.2 (sm_103a)"; }
+
+extern "C" const char *wect_last_stencil_kernel(void)
+{
+    switch (g_last_stencil.load()) {
+    case 1: return "cubical_fwd_kernel";
+    case 2: return "cubical_run_kernel";
+    case 3: return "cubical_fwd_kernel (global histogram)";
+    default: return "";
+    }
+}
 extern "C" int64_t wect_kernel_launch_count(void) { return g_launches.load(); }
 
 extern "C" wect_status wect_debug_fail_alloc(int64_t k)

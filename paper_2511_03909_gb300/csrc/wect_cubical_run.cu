@@ -19,6 +19,14 @@
 //     found by bisection on exact float64 bins.
 // Directions with s_0 < 0 walk the row from its far end.  Lanes map to directions sorted by
 // |s_0|, so the lanes of a warp walk similar numbers of boundaries.
+//
+// Measured against the per-vertex kernel on the 128^3 u8 volume, 256 Fibonacci directions: the
+// per-row set-up (octant contributions, prefix sums, end bins, enclosure constants) is a chain
+// of dependent steps between row-group barriers and costs ~140 us in all, and each boundary
+// costs more than a vertex update of the per-vertex kernel (the walks diverge across lanes and
+// the warps of a row group wait for the longest walk).  So this kernel wins only with a few
+// boundaries per long row (T = 8: 178 us against 267 us) and loses at T = 128 (827 us against
+// 203 us); the host takes it only in that regime.
 #include "wect_cubical_common.cuh"
 #include "wect_device.cuh"
 #include "wect_launch.h"
