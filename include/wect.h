@@ -273,9 +273,21 @@ WECT_API wect_status wect_batch_backward(wect_batch b, const double *dirs, int d
 WECT_API wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                              const double *G, float *grad_w, wect_stream stream);
 
-/* Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest. */
+/*
+ * Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest:
+ * for the per-vertex stencil kernel every tile width Dt (32 .. 32 x directions per lane x warps),
+ * 1, 2 or 4 directions per lane, and CTAs of 512 or 256 threads; for the run-based kernel (one
+ * histogram plane) Dt = 32 .. 256.  When no shared-histogram shape fits T, the global-histogram
+ * shape stays.  wect_batch_tuned_shape reports the choice.
+ */
 WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                 int64_t *scratch_out, wect_stream stream);
+
+/*
+ * The tile shape wect_batch_autotune chose for (d, T) (host int[4]): directions per lane, tile
+ * width, 1 for the run-based stencil kernel (else 0), CTA size; all zero when (d, T) is not tuned.
+ */
+WECT_API wect_status wect_batch_tuned_shape(wect_batch b, int d, int T, int *shape4);
 
 WECT_API void wect_batch_destroy(wect_batch b);
 

@@ -88,6 +88,7 @@ def _declare(L):
         "wect_batch_backward": (_st, [_p, _p, _i, _i, _d, _d, _p, _d, _p, _p]),
         "wect_batch_backward_f64": (_st, [_p, _p, _i, _i, _d, _d, _p, _p, _p]),
         "wect_batch_autotune": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
+        "wect_batch_tuned_shape": (_st, [_p, _i, _i, _p]),
         "wect_batch_destroy": (None, [_p]),
         "wect_last_error": (C.c_char_p, []),
         "wect_version": (C.c_char_p, []),
@@ -115,7 +116,7 @@ def exported_symbols():
         "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
-        "wect_batch_autotune",
+        "wect_batch_autotune", "wect_batch_tuned_shape",
         "wect_batch_destroy", "wect_last_error", "wect_version", "wect_last_stencil_kernel", "wect_kernel_launch_count",
         "wect_profile_enable", "wect_profile_read", "wect_cubical_compute_static", "wect_cubical_static_status",
         "wect_debug_fail_alloc", "wect_debug_stencil_variant",
@@ -417,6 +418,13 @@ class CubicalBatch:
     def autotune(self, dirs: torch.Tensor, T: int, lo: float, hi: float):
         scratch = torch.empty((self.count, dirs.shape[0], T), dtype=torch.int64, device=dirs.device)
         _check(load().wect_batch_autotune(self._h, _ptr(dirs), dirs.shape[0], T, lo, hi, _ptr(scratch), _stream()))
+
+    def tuned_shape(self, d: int, T: int):
+        """(directions per lane, tile width, run kernel, CTA size) chosen by autotune for (d, T),
+        or None when (d, T) is not tuned."""
+        buf = (C.c_int * 4)()
+        _check(load().wect_batch_tuned_shape(self._h, int(d), int(T), buf))
+        return None if buf[1] == 0 else (int(buf[0]), int(buf[1]), bool(buf[2]), int(buf[3]))
 
     def backward(self, dirs: torch.Tensor, T: int, lo: float, hi: float, dW: torch.Tensor, scale: float,
                  grad: torch.Tensor | None = None) -> torch.Tensor:

@@ -150,6 +150,16 @@ static size_t smem_per_sm()
     return (size_t)v;
 }
 
+// CTAs per SM that a grid is sized for: the shared-memory and thread-slot limits.  Registers may
+// allow fewer to be resident; the kernels are persistent (work queue), so CTAs that start later
+// find the remaining items or none.
+static int ctas_per_sm_for(size_t smem, int threads)
+{
+    int k = (int)(smem_per_sm() / (smem + 2048));
+    k = std::min(k, 2048 / threads);
+    return std::max(1, k);
+}
+
 // ------------------------------------------------------------------ device buffers
 
 template <class T>
@@ -262,6 +272,7 @@ struct GraphEntry {
 struct BatchConfig {
     int dpl = 0, Dt = 0;
     bool run = false;             // the run-based kernel (dpl 1)
+    int threads = 512;            // CTA size of the per-vertex kernel
 };
 
 struct wect_batch_s {
@@ -342,7 +353,9 @@ struct CubShape {
     size_t smem;
     bool gh = false;              // global-histogram variant (T x Dt does not fit shared memory)
     bool run = false;             // run-based kernel (walks bin boundaries along the rows)
+    int threads = 512;            // CTA size
 };
+
 
 // Stencil variant selection: 0 = by cost estimate, 1 = per-vertex kernel only, 2 = the run-based
 // kernel wherever it applies (test hook wect_debug_stencil_variant).
@@ -378,10 +391,11 @@ static bool run_shape(int n, int d, int T, int maxL0, CubShape &out, int Dt_req 
         out.dpl = 1;
         out.Dt = Dt;
         out.smem = sm;
-        out.ctas_per_sm = std::max(1, std::min((int)(smem_per_sm() / (sm + 2048)), 2048 / cubical_run_threads()));
+        out.ctas_per_sm = ctas_per_sm_for(sm, cubical_run_threads());
         out.grid = sm_count() * out.ctas_per_sm;
         out.gh = false;
         out.run = true;
+        out.threads = cubical_run_threads();
         return true;
     }
     return false;
@@ -392,10 +406,11 @@ static bool run_shape(int n, int d, int T, int maxL0, CubShape &out, int Dt_req 
 // With run_ok (one histogram plane) the run-based kernel is taken when it is estimated cheaper
 // (meanL0 rows, a threshold range of width span), or always under the test hook.
 static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0,
-                      double meanL0 = 0.0, double span = 0.0)
+                      double meanL0 = 0.0, double span = 0.0, int threads_req = 0)
 {
-    const int threads = cubical_fwd_threads();
+    const int threads = threads_req > 0 ? threads_req : cubical_fwd_threads();
     const int warps = threads / 32;
+    out.threads = threads;
     const size_t limit = smem_optin() - 1024;
     out.run = false;
     if (nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1) {
@@ -413,13 +428,12 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
             const int WC = Dt / (32 * dpl);
             if (WC > warps || warps % WC) continue;
             if (dpl > 1 && Dt / dpl < 32) continue;
-            const size_t sm = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0);
+            const size_t sm = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0, false, threads);
             if (sm > limit) continue;
             out.dpl = dpl;
             out.Dt = Dt;
             out.smem = sm;
-            int k = (int)(smem_per_sm() / (sm + 2048));
-            k = std::max(1, std::min(k, 2048 / threads));
+            const int k = ctas_per_sm_for(sm, threads);
             out.ctas_per_sm = k;
             out.grid = sm_count() * k;
             out.gh = false;
@@ -432,10 +446,9 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     const int Dt = std::min(Dmax, 256);
     out.dpl = Dt >= 64 ? 2 : 1;
     out.Dt = Dt;
-    out.smem = cubical_fwd_smem(n, 1, out.dpl, T, Dt, maxL0, true);
+    out.smem = cubical_fwd_smem(n, 1, out.dpl, T, Dt, maxL0, true, threads);
     if (out.smem > limit) return false;
-    int k = (int)(smem_per_sm() / (out.smem + 2048));
-    k = std::max(1, std::min(k, 2048 / threads));
+    const int k = ctas_per_sm_for(out.smem, threads);
     out.ctas_per_sm = k;
     out.grid = sm_count() * k;
     out.gh = true;
@@ -521,6 +534,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.climit = L.climit;
     a.direct = direct ? 1 : 0;
     a.out = reinterpret_cast<unsigned long long *>(out);
+    a.threads = sh.threads;
     const int grid = std::max(1, std::min(sh.grid, n_items));
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1400,13 +1414,17 @@ static bool batch_shape(wect_batch b, int d, int T, double span, CubShape &sh)
     auto it = b->tuned.find({d, T});
     if (it != b->tuned.end()) {
         if (it->second.run) return b->nsplit == 1 && run_shape(b->n, d, T, b->maxL0, sh, it->second.Dt);
-        return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt);
+        return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt, 0.0, 0.0,
+                         it->second.threads);
     }
     return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span);
 }
 
 // Tile-shape code for cache keys: dpl, negative for the global-histogram variant, 100 for runs.
-static int shape_code(const CubShape &sh) { return sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1); }
+static int shape_code(const CubShape &sh)
+{
+    return sh.run ? 100 : (sh.dpl * (sh.gh ? -1 : 1) + (sh.threads == 256 ? 1000 : 0));
+}
 
 // Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
 // directly) when every complex fits one flush; otherwise row chunks balanced over the grid.
@@ -1544,6 +1562,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.climit = b->climit;
         a.direct = 0;
         a.out = reinterpret_cast<unsigned long long *>(out);
+        a.threads = sh.threads;
         const int grid = std::max(1, std::min(sh.grid, a.n_items));
         KL(sh.run ? launch_cubical_run(b->n, a, grid, sh.smem, st)
                   : launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st),
@@ -1611,23 +1630,26 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     std::lock_guard<std::mutex> lk(b->mu);
     if ((s = ensure_common_ws(b->ws, T, d))) return s;
     const int warps = cubical_fwd_threads() / 32;
-    // candidates: (directions per lane, tile width, run-based kernel)
-    std::vector<std::tuple<int, int, bool>> cands;
-    for (int dpl : {1, 2, 4})
-        for (int Dt = 32 * dpl; Dt <= 32 * dpl * warps; Dt *= 2) cands.push_back({dpl, Dt, false});
+    // candidates: (directions per lane, tile width, run-based kernel, CTA size)
+    std::vector<std::tuple<int, int, bool, int>> cands;
+    for (int threads : {512, 256})
+        for (int dpl : {1, 2, 4})
+            for (int Dt = 32 * dpl; Dt <= 32 * dpl * (threads / 32); Dt *= 2) cands.push_back({dpl, Dt, false, threads});
     if (b->nsplit == 1)
-        for (int Dt = 32; Dt <= 256; Dt *= 2) cands.push_back({1, Dt, true});
+        for (int Dt = 32; Dt <= 256; Dt *= 2) cands.push_back({1, Dt, true, cubical_run_threads()});
+    (void)warps;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     float best = 1e30f;
-    BatchConfig bc{0, 0, false};
-    for (auto [dpl, Dt, run] : cands) {
+    BatchConfig bc{0, 0, false, 512};
+    for (auto [dpl, Dt, run, threads] : cands) {
         if (Dt > 2 * std::max(d, 32 * dpl)) continue;
         CubShape sh;
         if (run) {
             if (!run_shape(b->n, d, T, b->maxL0, sh, Dt)) continue;
-        } else if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt) || sh.Dt != Dt || sh.dpl != dpl) {
+        } else if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt, 0.0, 0.0, threads) || sh.Dt != Dt ||
+                   sh.dpl != dpl) {
             continue;
         }
         bool direct = false;
@@ -1645,7 +1667,7 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
         if (s) break;
         if (ms_best < best) {
             best = ms_best;
-            bc = BatchConfig{dpl, Dt, run};
+            bc = BatchConfig{dpl, Dt, run, threads};
         }
     }
     cudaEventDestroy(e0);
@@ -1664,6 +1686,22 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     }
     b->graphs.clear();
     b->ws.items_key = std::make_tuple(-1, -1, -1, -1, -1);
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_batch_tuned_shape(wect_batch b, int d, int T, int *shape4)
+{
+    if (!b || !shape4) return fail(WECT_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(b->mu);
+    auto it = b->tuned.find({d, T});
+    if (it == b->tuned.end()) {
+        shape4[0] = shape4[1] = shape4[2] = shape4[3] = 0;
+        return WECT_OK;
+    }
+    shape4[0] = it->second.dpl;
+    shape4[1] = it->second.Dt;
+    shape4[2] = it->second.run ? 1 : 0;
+    shape4[3] = it->second.threads;
     return WECT_OK;
 }
 

@@ -413,7 +413,8 @@ static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, 
         done = smem;
     }
     if (!launch) return cudaSuccess;
-    cubical_fwd_kernel<N, NSPLIT, DPL, GH><<<grid, kFwdThreads, smem, st>>>(a);
+    const int threads = (a.threads > 0 && a.threads <= kFwdThreads) ? a.threads : kFwdThreads;
+    cubical_fwd_kernel<N, NSPLIT, DPL, GH><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -469,20 +470,21 @@ int cubical_fwd_pitch(int maxL0)
 }
 
 // gh: no shared histogram (the global-histogram variant, one row plane).
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh)
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh, int threads)
 {
+    if (threads <= 0 || threads > kFwdThreads) threads = kFwdThreads;
     if (gh) {
         nsplit = 1;
         T = 0;
     }
     const int noct = 1 << n;
     const int WC = Dt / (32 * dpl);
-    const int RG = (kFwdThreads / 32) / WC;
+    const int RG = (threads / 32) / WC;
     const size_t rowbuf = (size_t)nsplit * noct * cubical_fwd_pitch(maxL0);
     const int nbuf = (WC == 1) ? 1 : 2;
     // + one 32-entry fix-up queue per warp
     return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u +
-           (size_t)(kFwdThreads / 32) * 32u * 4u;
+           (size_t)(threads / 32) * 32u * 4u;
 }
 
 int cubical_fwd_threads() { return kFwdThreads; }

@@ -24,6 +24,7 @@ struct CubicalFwdArgs {
     int64_t climit;               // largest |c_o(v)| the accumulator mode supports
     int direct;                   // items cover whole complexes: scan in the CTA and store W
     unsigned long long *out;      // int64 difference tables (or W when direct) [count][d][T]
+    int threads;                  // CTA size of the per-vertex stencil kernel (256 or 512; 0 = 512)
 };
 
 struct CubicalBwdArgs {
@@ -92,9 +93,9 @@ static_assert(kWinBytes % 16 == 0 && kIdBytes % 16 == 0 && kWtBytes % 16 == 0, "
 cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, bool gh, const CubicalFwdArgs &a, int grid, size_t smem,
                                cudaStream_t st);
 cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, bool gh, size_t smem);   // dynamic smem attribute, outside capture
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh = false);
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh = false, int threads = 0);
 int cubical_fwd_pitch(int maxL0);
-int cubical_fwd_threads();
+int cubical_fwd_threads();           // the largest CTA size of the per-vertex stencil kernel
 // The adjoint's octant sums for one direction chunk, then (once every chunk is summed) the routing.
 // The run-based stencil kernel (one int32 histogram plane; directions in the run order of
 // launch_fwd_prep; CP = cubical_run_pitch): same arguments and items as launch_cubical_fwd.
