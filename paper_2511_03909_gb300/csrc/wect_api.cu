@@ -225,6 +225,7 @@ struct wect_complex_s {
     size_t wbytes = 0;             // bytes per raw vertex weight
     int32_t *d_w32 = nullptr;      // cubical: int32 fixed-point vertex weights read by the kernels
     double *d_xg = nullptr;        // cubical: grid coordinates [L0 + L1 + L2]
+    void *d_tmap = nullptr;        // cubical: TMA tensor map of d_w32 (null when the grid does not qualify)
     int nsplit = 1;
     int64_t climit = 0;            // cubical: max |c_o(v)|; simplicial: max |w(s)|
     int kflush = 1 << 16;
@@ -292,6 +293,8 @@ struct wect_batch_s {
     int *d_status = nullptr;
     int32_t *d_w32 = nullptr;      // owned concatenated int32 weights (create_cubical), else nullptr
     double *d_xg = nullptr;        // owned grid-coordinate tables (create_cubical), else nullptr
+    void *d_tmaps = nullptr;       // owned TMA tensor maps of the grids (create_cubical), else nullptr
+    bool has_tmap = false;         // some grid has a tensor map
     bool owns_w = false;
     Workspace ws;
     std::map<std::pair<int, int>, BatchConfig> tuned;    // (d, T) -> tile shape
@@ -354,11 +357,13 @@ struct CubShape {
     bool gh = false;              // global-histogram variant (T x Dt does not fit shared memory)
     bool run = false;             // run-based kernel (walks bin boundaries along the rows)
     int threads = 512;            // CTA size
+    int L0s = 0;                  // > 0: TMA staging of the neighbouring rows (per-vertex kernel)
 };
 
 
 // Stencil variant selection: 0 = by cost estimate, 1 = per-vertex kernel only, 2 = the run-based
-// kernel wherever it applies (test hook wect_debug_stencil_variant).
+// kernel wherever it applies, 3 = per-vertex kernel without TMA row staging (test hook
+// wect_debug_stencil_variant).
 static std::atomic<int> g_stencil_variant{0};
 
 // Should a grid with rows of L0 vertices (mean) take the run-based kernel for T thresholds over a
@@ -406,14 +411,18 @@ static bool run_shape(int n, int d, int T, int maxL0, CubShape &out, int Dt_req 
 // With run_ok (one histogram plane) the run-based kernel is taken when it is estimated cheaper
 // (meanL0 rows, a threshold range of width span), or always under the test hook.
 static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0,
-                      double meanL0 = 0.0, double span = 0.0, int threads_req = 0)
+                      double meanL0 = 0.0, double span = 0.0, int threads_req = 0, bool tma_ok = false)
 {
     const int threads = threads_req > 0 ? threads_req : cubical_fwd_threads();
     const int warps = threads / 32;
     out.threads = threads;
+    out.L0s = 0;
+    // TMA staging of the neighbouring rows when some grid has a tensor map and it fits next to
+    // the histogram (else plain loads)
+    const int L0s = (tma_ok && g_stencil_variant.load() != 3) ? cubical_fwd_stage_len(n, maxL0) : 0;
     const size_t limit = smem_optin() - 1024;
     out.run = false;
-    if (nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1) {
+    if (nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1 && g_stencil_variant.load() != 3) {
         const bool want = g_stencil_variant.load() == 2 ||
                           run_profitable(n, meanL0 > 0.0 ? meanL0 : (double)maxL0, T, span);
         if (want && run_shape(n, d, T, maxL0, out)) return true;
@@ -428,8 +437,15 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
             const int WC = Dt / (32 * dpl);
             if (WC > warps || warps % WC) continue;
             if (dpl > 1 && Dt / dpl < 32) continue;
-            const size_t sm = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0, false, threads);
+            size_t sm = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0, false, threads);
             if (sm > limit) continue;
+            if (L0s > 0) {
+                const size_t smt = cubical_fwd_smem(n, nsplit, dpl, T, Dt, maxL0, false, threads, L0s);
+                if (smt <= limit) {
+                    sm = smt;
+                    out.L0s = L0s;
+                }
+            }
             out.dpl = dpl;
             out.Dt = Dt;
             out.smem = sm;
@@ -448,6 +464,13 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     out.Dt = Dt;
     out.smem = cubical_fwd_smem(n, 1, out.dpl, T, Dt, maxL0, true, threads);
     if (out.smem > limit) return false;
+    if (L0s > 0) {
+        const size_t smt = cubical_fwd_smem(n, 1, out.dpl, T, Dt, maxL0, true, threads, L0s);
+        if (smt <= limit) {
+            out.smem = smt;
+            out.L0s = L0s;
+        }
+    }
     const int k = ctas_per_sm_for(out.smem, threads);
     out.ctas_per_sm = k;
     out.grid = sm_count() * k;
@@ -535,6 +558,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.direct = direct ? 1 : 0;
     a.out = reinterpret_cast<unsigned long long *>(out);
     a.threads = sh.threads;
+    a.L0s = sh.L0s;
     const int grid = std::max(1, std::min(sh.grid, n_items));
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -668,6 +692,15 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
         append_grid_coords(c->L, xg);
         if ((e = upload_doubles(xg, &c->d_xg, st))) return cleanup(cuda_fail(e, "grid coordinates"));
     }
+    {
+        // TMA tensor map of the int32 weights, for grids that qualify (rows of a multiple of 4
+        // vertices, at most 256)
+        alignas(64) unsigned char map[128];
+        if (encode_grid_tmap(n, c->L, c->d_w32, map)) {
+            if ((e = dev_malloc(&c->d_tmap, sizeof map))) return cleanup(cuda_fail(e, "alloc tensor map"));
+            if ((e = cudaMemcpy(c->d_tmap, map, sizeof map, cudaMemcpyHostToDevice))) return cleanup(cuda_fail(e, "tensor map"));
+        }
+    }
     GridDesc g{};
     g.w = c->d_w32;
     for (int a = 0; a < 3; ++a) g.L[a] = c->L[a];
@@ -676,6 +709,7 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     g.v_off = 0;
     g.status = c->d_status;
     g.xg = c->d_xg;
+    g.tmap = c->d_tmap;
     e = dev_malloc((void **)&c->d_grid, sizeof(GridDesc));
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_grid, &g, sizeof g, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -847,6 +881,7 @@ extern "C" void wect_complex_destroy(wect_complex c)
     cudaDeviceSynchronize();
     if (c->d_w32) cudaFree(c->d_w32);
     if (c->d_xg) cudaFree(c->d_xg);
+    if (c->d_tmap) cudaFree(c->d_tmap);
     if (c->d_coords) cudaFree(c->d_coords);
     if (c->d_xf) cudaFree(c->d_xf);
     for (int i = 0; i <= kMaxSimplexDim; ++i) {
@@ -933,7 +968,7 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
                                    cudaStream_t st)
 {
     CubShape sh;
-    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh, 0, 0, (double)c->L[0], hi - lo))
+    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh, 0, 0, (double)c->L[0], hi - lo, 0, c->d_tmap != nullptr))
         return fail(WECT_ERR_UNSUPPORTED, "grid rows of %d vertices do not fit the kernel's shared row buffers", c->L[0]);
     if (c->L[0] > c->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
     wect_status s = ensure_common_ws(c->ws, T, d);
@@ -941,7 +976,7 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
     const int rows = c->L[1] * c->L[2];
     const bool direct = false;
     auto key = std::make_tuple(d, T, sh.Dt, sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1), sh.grid);
-    if (c->ws.items_key != key) {
+    if (c->ws.items_key != key) {   // (items do not depend on the TMA staging)
         std::vector<GridDesc> gv(1);
         gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
         gv[0].rows = rows;
@@ -1299,6 +1334,8 @@ extern "C" wect_status wect_batch_create(int count, const wect_complex *cxs, wec
         g.nv = cxs[i]->nv;
         g.status = cxs[i]->d_status;
         g.xg = cxs[i]->d_xg;
+        g.tmap = cxs[i]->d_tmap;
+        b->has_tmap = b->has_tmap || g.tmap != nullptr;
         b->h_grids[i] = g;
     }
     cudaError_t e = dev_malloc((void **)&b->d_status, sizeof(int));
@@ -1365,6 +1402,29 @@ extern "C" wect_status wect_batch_create_cubical(int count, int n, const int64_t
         b->h_grids[i].status = b->d_status;
         off += b->h_grids[i].nv;
     }
+    {
+        // TMA tensor maps of the grids that qualify (16-byte aligned start, rows of a multiple of
+        // 4 vertices, at most 256), 128 bytes each in one device array
+        std::vector<unsigned char> maps;
+        std::vector<int> which(count, -1);
+        for (int i = 0; i < count; ++i) {
+            alignas(64) unsigned char map[128];
+            if (encode_grid_tmap(n, b->h_grids[i].L, b->h_grids[i].w, map)) {
+                which[i] = (int)(maps.size() / 128);
+                maps.insert(maps.end(), map, map + 128);
+            }
+        }
+        if (!maps.empty()) {
+            if ((e = dev_malloc(&b->d_tmaps, maps.size()))) { wect_batch_destroy(b); return cuda_fail(e, "alloc tensor maps"); }
+            if ((e = cudaMemcpy(b->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice))) {
+                wect_batch_destroy(b);
+                return cuda_fail(e, "tensor maps");
+            }
+            for (int i = 0; i < count; ++i)
+                if (which[i] >= 0) b->h_grids[i].tmap = static_cast<unsigned char *>(b->d_tmaps) + 128 * which[i];
+            b->has_tmap = true;
+        }
+    }
     if ((s = batch_finish(b, st))) { wect_batch_destroy(b); return s; }
     uint64_t wmax = 255;
     if (wtype == WECT_W_F32 || wtype == WECT_W_I64_FIXED) {
@@ -1415,15 +1475,15 @@ static bool batch_shape(wect_batch b, int d, int T, double span, CubShape &sh)
     if (it != b->tuned.end()) {
         if (it->second.run) return b->nsplit == 1 && run_shape(b->n, d, T, b->maxL0, sh, it->second.Dt);
         return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt, 0.0, 0.0,
-                         it->second.threads);
+                         it->second.threads, b->has_tmap);
     }
-    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span);
+    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span, 0, b->has_tmap);
 }
 
 // Tile-shape code for cache keys: dpl, negative for the global-histogram variant, 100 for runs.
 static int shape_code(const CubShape &sh)
 {
-    return sh.run ? 100 : (sh.dpl * (sh.gh ? -1 : 1) + (sh.threads == 256 ? 1000 : 0));
+    return sh.run ? 100 : (sh.dpl * (sh.gh ? -1 : 1) + (sh.threads == 256 ? 1000 : 0) + (sh.L0s > 0 ? 10000 : 0));
 }
 
 // Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
@@ -1563,6 +1623,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.direct = 0;
         a.out = reinterpret_cast<unsigned long long *>(out);
         a.threads = sh.threads;
+        a.L0s = sh.L0s;
         const int grid = std::max(1, std::min(sh.grid, a.n_items));
         KL(sh.run ? launch_cubical_run(b->n, a, grid, sh.smem, st)
                   : launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st),
@@ -1648,8 +1709,8 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
         CubShape sh;
         if (run) {
             if (!run_shape(b->n, d, T, b->maxL0, sh, Dt)) continue;
-        } else if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt, 0.0, 0.0, threads) || sh.Dt != Dt ||
-                   sh.dpl != dpl) {
+        } else if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, dpl, Dt, 0.0, 0.0, threads, b->has_tmap) ||
+                   sh.Dt != Dt || sh.dpl != dpl) {
             continue;
         }
         bool direct = false;
@@ -1676,7 +1737,8 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     if (bc.Dt == 0) {
         // no shared-histogram shape fits this T: compute keeps the global-histogram shape
         CubShape sh;
-        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh)) return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
+        if (!cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, 0.0, 0.0, 0, b->has_tmap))
+            return fail(WECT_ERR_UNSUPPORTED, "no tile shape fits");
         return WECT_OK;
     }
     b->tuned[{d, T}] = bc;
@@ -1707,7 +1769,7 @@ extern "C" wect_status wect_batch_tuned_shape(wect_batch b, int d, int T, int *s
 
 extern "C" wect_status wect_debug_stencil_variant(int variant)
 {
-    if (variant < 0 || variant > 2) return fail(WECT_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 3) return fail(WECT_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
     g_stencil_variant.store(variant);
     return WECT_OK;
 }
@@ -1724,6 +1786,7 @@ extern "C" void wect_batch_destroy(wect_batch b)
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_status) cudaFree(b->d_status);
     if (b->owns_w && b->d_w32) cudaFree(b->d_w32);
+    if (b->d_tmaps) cudaFree(b->d_tmaps);
     if (b->d_xg) cudaFree(b->d_xg);
     b->ws.release();
     delete b;

@@ -21,6 +21,10 @@
 // T x Dt int32 entries no longer fit shared memory (large T), the GH variant scatters every
 // update straight into the int64 difference table in global memory instead (same bins, same
 // integer sums; slower, but any T).
+#include <cuda.h>
+
+#include <mutex>
+
 #include "wect_cubical_common.cuh"
 #include "wect_device.cuh"
 #include "wect_launch.h"
@@ -254,8 +258,10 @@ template <int N, int NSPLIT, int DPL, bool GH>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
 {
     constexpr int NOCT = 1 << N;
+    constexpr int NROWS = (N >= 3) ? 9 : (N == 2 ? 3 : 1);      // neighbouring rows of a box
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
+    __shared__ __align__(8) unsigned long long s_mbar[16][2];    // TMA completion, per row group
     const int T = P.T, Dt = P.Dt, CP = P.CP;
     const int histWords = GH ? 0 : T * Dt;      // GH: no shared histogram
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -273,6 +279,21 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     const uint32_t histAddr = smem_addr(hist);
     const uint32_t HOFF = (uint32_t)histWords * 4u;
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
+    // TMA staging of the neighbouring rows: two boxes per row group, each NROWS rows of up to
+    // L0s int32 (128-byte aligned), filled by the group's first thread one row ahead
+    const uint32_t rawEnd = smem_addr(wq - wid * 32 + nwarps * 32);       // end of the fix-up queues
+    const uint32_t stageAddr = (rawEnd + 127u) & ~127u;                      // 128-byte aligned in shared space
+    int32_t *stage = reinterpret_cast<int32_t *>(smem + (stageAddr - smem_addr(smem))) +
+                     (size_t)rgroup * 2 * NROWS * P.L0s;
+    const uint32_t mbar0 = smem_addr(&s_mbar[rgroup][0]), mbar1 = smem_addr(&s_mbar[rgroup][1]);
+    if (P.L0s > 0 && tid == 0) {
+        for (int gi = 0; gi < RG; ++gi) {
+            mbar_init(smem_addr(&s_mbar[gi][0]), 1);
+            mbar_init(smem_addr(&s_mbar[gi][1]), 1);
+        }
+        mbar_fence_init();
+    }
+    unsigned krow = 0;                      // rows this group has staged (buffer krow & 1, phase krow >> 1)
 
     for (int i = tid; i < NSPLIT * histWords; i += blockDim.x) hist[i] = 0;
 
@@ -320,14 +341,36 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 
         // ---- each row group walks rows r0 + rgroup, r0 + rgroup + RG, ... with a double-buffered
         // row of octant contributions (one group barrier per row, no block-wide barrier)
+        const bool tma = (N >= 2) && P.L0s > 0 && g.tmap != nullptr;
+        const uint32_t boxBytes = (uint32_t)(NROWS * L0) * 4u;
+        // box of the rows around row r' (rows outside the grid come back as zeros)
+        auto stage_row = [&](int rr, unsigned kb) {
+            const uint32_t mb = (kb & 1u) ? mbar1 : mbar0;
+            mbar_arrive_expect_tx(mb, boxBytes);
+            tma_load_3d(smem_addr(stage + (size_t)(kb & 1u) * NROWS * P.L0s), g.tmap, 0, rr % L1 - 1,
+                        N >= 3 ? rr / L1 - 1 : 0, mb);
+        };
+        if (tma && gtid == 0 && W.r0 + rgroup < W.r1) stage_row(W.r0 + rgroup, krow);
         int parity = 0;
         for (int r = W.r0 + rgroup; r < W.r1; r += RG, parity ^= 1) {
             int32_t *crow = cgrp + (nbuf == 2 ? parity : 0) * rowbuf;
             if (nbuf == 1) __syncwarp();        // the previous row's reads are done before the rewrite
             const int i1 = r % L1, i2 = r / L1;
+            const unsigned k = krow;
+            const int32_t *box = stage + (size_t)(k & 1u) * NROWS * P.L0s;
+            if (tma) {
+                ++krow;
+                // the next row's box into the other buffer (its last reader finished before the
+                // previous row's group barrier), then wait for this row's
+                if (gtid == 0 && r + RG < W.r1) stage_row(r + RG, k + 1);
+                if (!mbar_wait_bounded((k & 1u) ? mbar1 : mbar0, (k >> 1) & 1u)) atomicOr(g.status, kStatusTimeout);
+            }
             for (int i0 = gtid; i0 < L0; i0 += gthreads) {
                 int32_t c[NOCT];
-                octant_contribs<N>(g, i0, i1, i2, c);
+                if (tma)
+                    octant_contribs_box<N>(box, g, i0, i1, i2, c);
+                else
+                    octant_contribs<N>(g, i0, i1, i2, c);
 #pragma unroll
                 for (int o = 0; o < NOCT; ++o) {
                     const int32_t v = c[o];
@@ -470,7 +513,12 @@ int cubical_fwd_pitch(int maxL0)
 }
 
 // gh: no shared histogram (the global-histogram variant, one row plane).
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh, int threads)
+int cubical_fwd_stage_len(int n, int maxL0)
+{
+    return (n >= 2 && maxL0 <= 256) ? (maxL0 + 31) & ~31 : 0;
+}
+
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh, int threads, int L0s)
 {
     if (threads <= 0 || threads > kFwdThreads) threads = kFwdThreads;
     if (gh) {
@@ -483,11 +531,58 @@ size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bo
     const size_t rowbuf = (size_t)nsplit * noct * cubical_fwd_pitch(maxL0);
     const int nbuf = (WC == 1) ? 1 : 2;
     // + one 32-entry fix-up queue per warp
-    return (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u +
-           (size_t)(threads / 32) * 32u * 4u;
+    size_t sz = (size_t)nsplit * T * Dt * 4u + (size_t)Dt * sizeof(DirFilter) + (size_t)RG * nbuf * rowbuf * 4u +
+                (size_t)(threads / 32) * 32u * 4u;
+    if (L0s > 0) {            // TMA staging: 128-byte aligned, two boxes of 3^(n-1) rows per row group
+        const int nrows = n >= 3 ? 9 : (n == 2 ? 3 : 1);
+        sz += 128u + (size_t)RG * 2u * nrows * L0s * 4u;      // + room to align the staging area
+    }
+    return sz;
 }
 
 int cubical_fwd_threads() { return kFwdThreads; }
+
+// ------------------------------------------------------------------ TMA tensor maps
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link against libcuda).
+static EncodeTiledFn encode_tiled()
+{
+    static std::mutex mu;
+    static bool tried = false;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool encode_grid_tmap(int n, const int *dims, const int32_t *w, void *map)
+{
+    // rows of 16-byte multiples (x stays aligned at 0), a box of at most 256 along every axis,
+    // at least three rows per axis the box spans
+    if (n < 2 || dims[0] % 4 != 0 || dims[0] > 256 || dims[1] < 3 || (n >= 3 && dims[2] < 3)) return false;
+    if (reinterpret_cast<uintptr_t>(w) & 15u) return false;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)(n >= 3 ? dims[2] : 1)};
+    const cuuint64_t gstride[2] = {(cuuint64_t)dims[0] * 4u, (cuuint64_t)dims[0] * (cuuint64_t)dims[1] * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)dims[0], 3u, n >= 3 ? 3u : 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = fn(reinterpret_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_INT32, 3,
+                          const_cast<int32_t *>(w), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 cudaError_t launch_grid_max_abs(int n, const GridDesc *grids, const double *dirs, int d, unsigned long long *Mbits,
                                 cudaStream_t st)

@@ -9,18 +9,18 @@ namespace wect {
 // ------------------------------------------------------------------ octant contributions
 
 // c_o(v) for every octant o from the int32 fixed-point weights of v's 3^n neighbourhood (the
-// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set).
-template <int N>
-__device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i1, int i2, int32_t *c /* [1 << N] */)
+// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set).  ld(dx, dy, dz)
+// returns the weight of vertex (i0 + dx, i1 + dy, i2 + dz); it is called only inside the grid.
+template <int N, class Load>
+__device__ __forceinline__ void octant_contribs_with(Load ld, int L0, int L1, int L2, int i0, int i1, int i2,
+                                                     int32_t *c /* [1 << N] */)
 {
     constexpr int NOCT = 1 << N;
     constexpr int NY = (N >= 2) ? 3 : 1;
     constexpr int NZ = (N >= 3) ? 3 : 1;
-    const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2];
     const bool ok0[3] = {i0 > 0, true, i0 < L0 - 1};
     const bool ok1[3] = {i1 > 0, true, i1 < L1 - 1};
     const bool ok2[3] = {i2 > 0, true, i2 < L2 - 1};
-    const int64_t v = (int64_t)i0 + (int64_t)L0 * ((int64_t)i1 + (int64_t)L1 * i2);
     // box maxima over the 3^n neighbourhood, axis by axis: A[z][y][x] = max over the box spanning
     // v and v + (x-1, y-1, z-1)
     int32_t A[NZ][NY][3];
@@ -33,7 +33,7 @@ __device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i
             for (int x = 0; x < 3; ++x) {
                 const int dy = (N >= 2) ? y - 1 : 0, dz = (N >= 3) ? z - 1 : 0;
                 const bool ok = ok0[x] && (N < 2 || ok1[y]) && (N < 3 || ok2[z]);
-                w[x] = ok ? __ldg(g.w + v + (x - 1) + (int64_t)L0 * (dy + (int64_t)L1 * dz)) : 0;
+                w[x] = ok ? ld(x - 1, dy, dz) : 0;
             }
             A[z][y][0] = max(w[0], w[1]);
             A[z][y][1] = w[1];
@@ -79,6 +79,29 @@ __device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i
         }
         c[o] = acc;
     }
+}
+
+// From the complex's int32 weights in global memory.
+template <int N>
+__device__ __forceinline__ void octant_contribs(const GridDesc &g, int i0, int i1, int i2, int32_t *c)
+{
+    const int L0 = g.L[0], L1 = g.L[1];
+    const int32_t *w = g.w + (int64_t)i0 + (int64_t)L0 * ((int64_t)i1 + (int64_t)L1 * i2);
+    octant_contribs_with<N>([&](int dx, int dy, int dz) { return __ldg(w + dx + (int64_t)L0 * (dy + (int64_t)L1 * dz)); },
+                            L0, L1, g.L[2], i0, i1, i2, c);
+}
+
+// From a staged box of the neighbouring rows: row (i1 + y - 1, i2 + z - 1) of the grid at
+// box + (z * NY + y) * L0 (rows outside the grid are zero and never read).
+template <int N>
+__device__ __forceinline__ void octant_contribs_box(const int32_t *box, const GridDesc &g, int i0, int i1, int i2,
+                                                    int32_t *c)
+{
+    constexpr int NY = (N >= 2) ? 3 : 1;
+    const int L0 = g.L[0];
+    const int32_t *b = box + i0;
+    octant_contribs_with<N>([&](int dx, int dy, int dz) { return b[((dz + (N >= 3 ? 1 : 0)) * NY + dy + (N >= 2 ? 1 : 0)) * L0 + dx]; },
+                            L0, g.L[1], g.L[2], i0, i1, i2, c);
 }
 
 // ------------------------------------------------------------------ forward helpers

@@ -42,6 +42,7 @@ struct GridDesc {
     int64_t v_off;       // vertex offset of this complex in concatenated per-vertex arrays
     int *status;         // device status word of the complex
     const double *xg;    // grid coordinates [L0 + L1 + L2] (axis 0, then 1, then 2), or null
+    const void *tmap;    // TMA tensor map of w as a 3-D [L2][L1][L0] int32 tensor, or null
 };
 
 // A unit of work of the cubical kernels: one complex, one direction tile, a row range.
@@ -297,6 +298,58 @@ __device__ __forceinline__ int4 lds128(uint32_t addr)
     int4 r;
     asm volatile("ld.shared.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(addr));
     return r;
+}
+
+// ------------------------------------------------------------------ TMA and mbarriers
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisations visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete, at most about 2^20 polls with a short
+// sleep between them (a few tens of milliseconds); false when the wait ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity)
+{
+    for (int k = 0; k < (1 << 20); ++k) {
+        if (mbar_test_wait(mbar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+// TMA tile load of a 3-D box at coordinates (x, y, z) of the tensor described by tmap (a tensor
+// map in global memory) into shared memory at dst, completing on the mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tmap, int x, int y, int z, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
 }
 
 // Round a signed 128-bit integer (hi:lo) to the nearest double, ties to even.

@@ -25,6 +25,8 @@ struct CubicalFwdArgs {
     int direct;                   // items cover whole complexes: scan in the CTA and store W
     unsigned long long *out;      // int64 difference tables (or W when direct) [count][d][T]
     int threads;                  // CTA size of the per-vertex stencil kernel (256 or 512; 0 = 512)
+    int L0s;                      // > 0: rows are staged by TMA from grids with a tensor map, into
+                                  // per-row-group buffers of 2 x 3^(n-1) rows of L0s int32
 };
 
 struct CubicalBwdArgs {
@@ -93,7 +95,14 @@ static_assert(kWinBytes % 16 == 0 && kIdBytes % 16 == 0 && kWtBytes % 16 == 0, "
 cudaError_t launch_cubical_fwd(int n, int nsplit, int dpl, bool gh, const CubicalFwdArgs &a, int grid, size_t smem,
                                cudaStream_t st);
 cudaError_t prepare_cubical_fwd(int n, int nsplit, int dpl, bool gh, size_t smem);   // dynamic smem attribute, outside capture
-size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh = false, int threads = 0);
+size_t cubical_fwd_smem(int n, int nsplit, int dpl, int T, int Dt, int maxL0, bool gh = false, int threads = 0,
+                        int L0s = 0);
+// Row length of the TMA staging buffers for grids whose rows are at most maxL0 long (0: no TMA).
+int cubical_fwd_stage_len(int n, int maxL0);
+// TMA tensor map of an int32 grid [dims[2]][dims[1]][dims[0]] at w (16-byte aligned, dims[0] a
+// multiple of 4 and at most 256, n >= 2), box {dims[0], 3, 3 or 1}, into host memory map (128
+// bytes, 64-byte aligned).  False when the grid does not qualify or encoding fails.
+bool encode_grid_tmap(int n, const int *dims, const int32_t *w, void *map);
 int cubical_fwd_pitch(int maxL0);
 int cubical_fwd_threads();           // the largest CTA size of the per-vertex stencil kernel
 // The adjoint's octant sums for one direction chunk, then (once every chunk is summed) the routing.

@@ -1,6 +1,7 @@
-"""The two stencil kernels of full cubical grids give identical integers: the per-vertex kernel
-and the run-based kernel (bin boundaries along the rows, prefix-sum differences), each forced
-through the wect_debug_stencil_variant hook, against the oracle."""
+"""The stencil kernels of full cubical grids give identical integers: the per-vertex kernel with
+and without TMA staging of the neighbouring rows, and the run-based kernel (bin boundaries along
+the rows, prefix-sum differences), each forced through the wect_debug_stencil_variant hook,
+against the oracle."""
 import math
 
 import numpy as np
@@ -72,13 +73,45 @@ def test_both_stencil_kernels_match_oracle(P, oracle, case):
     dirs = _dirs(n, d, case)
     vw = np.zeros(int(np.prod(dims)), dtype=np.int64) if w is None else w.ravel().astype(np.int64)
     ref = oracle.wect_cubical(dims, vw, dirs, T, lo, hi, weighted=w is not None)
-    for variant in (1, 2, 0):
+    for variant in (1, 2, 3, 0):
         P.stencil_variant(variant)
         cx = P.CubicalComplex(None if w is None else cuda(w), frac_bits=fb, dims=dims)
         got = cx.wect(cuda(dirs), T, lo, hi).cpu().numpy()
         cx.device_status()
         assert np.array_equal(got, ref), variant
     P.stencil_variant(0)
+
+
+def test_tma_staging_on_volumes(P, oracle):
+    """Grids with rows of 64 and 128 vertices (TMA staging applies) with u8, f32 and i64 weights,
+    with and without the staging, and a batch of volumes whose tensor maps are per grid."""
+    rng = np.random.default_rng(77)
+    dirs = S.fibonacci_directions(96)
+    for dims, kind in (([64, 20, 9], "u8"), ([128, 3, 5], "f32"), ([32, 7, 12], "i64"), ([48, 40], "u8")):
+        shape = tuple(reversed(dims))
+        if kind == "u8":
+            w, fb = rng.integers(0, 256, shape, dtype=np.uint8), 0
+        elif kind == "f32":
+            w, fb = rng.random(shape, dtype=np.float32), 24
+        else:
+            w, fb = rng.integers(-(1 << 20), 1 << 20, shape).astype(np.int64), 0
+        n = len(dims)
+        D = dirs if n == 3 else S.circle_directions(96)
+        lo, hi = -math.sqrt(n), math.sqrt(n)
+        ref = oracle.wect_cubical(dims, oracle.to_fixed(w, fb), D, 77, lo, hi)
+        for variant in (3, 1):
+            P.stencil_variant(variant)
+            cx = P.CubicalComplex(cuda(w), frac_bits=fb)
+            got = cx.wect(cuda(D), 77, lo, hi).cpu().numpy()
+            cx.device_status()
+            assert np.array_equal(got, ref), (dims, variant)
+    P.stencil_variant(0)
+    vols = S.uniform_f32_grids(6, [16, 12, 10], seed=78)
+    b = P.CubicalBatch([cuda(x) for x in vols], frac_bits=24)
+    got = b.wect(cuda(dirs), 40, -SQ3, SQ3).cpu().numpy()
+    for i in range(6):
+        ref = oracle.wect_cubical([16, 12, 10], oracle.to_fixed(vols[i], 24), dirs, 40, -SQ3, SQ3)
+        assert np.array_equal(got[i], ref), i
 
 
 def test_run_kernel_voxel_field_sampled(P, oracle):
