@@ -11,7 +11,8 @@ x d per step, summed over all ranks.
 
 The same JSON line also carries the metric's other two parts, each timed with CUDA events in a
 clock-sampled window of its own: "batched_vs_loop" (4096 blob images, d = 64, T = 64: one
-graph-captured persistent launch against the per-image launch loop) and "fwd_bwd_ratio" (256
+graph-captured persistent launch with the autotuned tile shape against the per-image launch
+loop) and "fwd_bwd_ratio" (256
 volumes of 64^3, d = 128, T = 128: autograd forward + MSE + backward against the forward), and
 "ecf_intensity" (the intensity-filter ECF of uniform 2048^2 .. 8192^2 images and 128^3 .. 512^3
 volumes at T = 1000 and 10000).
@@ -496,12 +497,16 @@ def secondary(P, S, dev, steps, flush, local):
     dirs = torch.from_numpy(wl.dirs).to(dev)
     b = P.CubicalBatch([torch.from_numpy(x).to(dev) for x in wl.grids])
     out = torch.empty((len(wl.grids), len(wl.dirs), wl.T), dtype=torch.int64, device=dev)
+    b.autotune(dirs, wl.T, wl.lo, wl.hi)            # the tile shape of the batched launch
+    shape = b.tuned_shape(len(wl.dirs), wl.T)
     t_batch, ck_b = _section(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out), steps, flush, local)
     t_loop, ck_l = _section(lambda: b.wect(dirs, wl.T, wl.lo, wl.hi, out=out, loop=True), min(steps, 5), flush, local,
                             warmup=1)
     cells = sum((2 * x.shape[0] - 1) * (2 * x.shape[1] - 1) for x in wl.grids)
     res["batched_vs_loop"] = {"workload": wl.name, "batched_ms": t_batch, "loop_ms": t_loop,
                               "ratio": t_loop / t_batch, "batched_evals_per_s": cells * len(wl.dirs) / (t_batch / 1e3),
+                              "tuned_shape": {"directions_per_lane": shape[0], "tile": shape[1], "run_kernel": shape[2],
+                                              "cta_threads": shape[3]} if shape else None,
                               "clocks_batched": ck_b, "clocks_loop": ck_l}
     del b, out
     # differentiation: 256 volumes 64^3 f32, d=128, T=128, MSE against a target batch
