@@ -201,15 +201,16 @@ struct Workspace {
     DBuf<double> gscale;          // its power-of-two scale
     DBuf<WorkItem> items;
     DBuf<WorkItem> items_bwd;
+    DBuf<int> ranges_bwd;         // per CTA of the octant sums: its first item (and the end)
     // cache key of the uploaded item list
     std::tuple<int, int, int, int, int> items_key{-1, -1, -1, -1, -1};
     std::tuple<int, int> items_bwd_key{-1, -1};
-    int n_items = 0, n_items_bwd = 0;
+    int n_items = 0, n_items_bwd = 0, n_ctas_bwd = 0;
     void release()
     {
         range.release(); beta.release(); M.release(); cand.release(); counter.release(); perm.release(); octb.release();
         bins.release(); dtab.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
-        items_bwd.release();
+        items_bwd.release(); ranges_bwd.release();
     }
 };
 
@@ -1175,19 +1176,42 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     const size_t sm = cubical_bwd_rsum_smem(n, dc, T, R);
     auto key = std::make_tuple(d, R);
     if (ws.items_bwd_key != key) {
+        // one CTA per SM (the suffix table fills shared memory), each taking a contiguous share of
+        // all rows with about the same number of vertices, cut at complex boundaries into items;
+        // a CTA stages a complex's suffix rows once for all its rows of that complex
+        int64_t total = 0;
+        for (int c = 0; c < n_grids; ++c) total += (int64_t)h_grids[c].rows * h_grids[c].L[0];
+        const int nctas = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(), total / 64));
         std::vector<WorkItem> items;
-        for (int c = 0; c < n_grids; ++c) {
-            const int rows = h_grids[c].rows;
-            // about 64K vertices per item: the shared suffix table is staged once per item
-            const int per = std::max(R, ((std::max(1, 65536 / std::max(1, h_grids[c].L[0])) + R - 1) / R) * R);
-            for (int r0 = 0; r0 < rows; r0 += per) items.push_back(WorkItem{c, 0, r0, std::min(rows, r0 + per)});
+        std::vector<int> ranges(1, 0);
+        int64_t done = 0;                   // vertices assigned so far
+        int c = 0, r = 0;
+        for (int b = 0; b < nctas; ++b) {
+            const int64_t goal = (b == nctas - 1) ? total : total * (b + 1) / nctas;
+            while (c < n_grids && done < goal) {
+                const int L0 = std::max(1, h_grids[c].L[0]);
+                const int rows = h_grids[c].rows;
+                const int take = (int)std::min<int64_t>(rows - r, std::max<int64_t>(1, (goal - done + L0 - 1) / L0));
+                items.push_back(WorkItem{c, 0, r, r + take});
+                done += (int64_t)take * L0;
+                r += take;
+                if (r >= rows) {
+                    ++c;
+                    r = 0;
+                }
+            }
+            ranges.push_back((int)items.size());
         }
         ws.items_bwd_key = std::make_tuple(-1, -1);         // set again once the upload is done
         ws.n_items_bwd = 0;
         CK(ws.items_bwd.ensure(items.size()), "alloc");
+        CK(ws.ranges_bwd.ensure(ranges.size()), "alloc");
         CK(cudaMemcpyAsync(ws.items_bwd.p, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st), "upload");
+        CK(cudaMemcpyAsync(ws.ranges_bwd.p, ranges.data(), ranges.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+           "upload");
         CK(cudaStreamSynchronize(st), "sync");
         ws.n_items_bwd = (int)items.size();
+        ws.n_ctas_bwd = nctas;
         ws.items_bwd_key = key;
     }
     const bool dflt = range_is_default(lo, hi);
@@ -1231,7 +1255,8 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
             a.d = dn;
             a.p0 = p0;
             a.accumulate = p0 > 0 ? 1 : 0;
-            KL(launch_cubical_bwd_rsum(n, a, ws.n_items_bwd, sm, st), "cubical_bwd_rsum");
+            a.item_ranges = ws.ranges_bwd.p;
+            KL(launch_cubical_bwd_rsum(n, a, ws.n_ctas_bwd, sm, st), "cubical_bwd_rsum");
         }
         KL(launch_cubical_bwd_route(n, a, st), "cubical_bwd_route");
     }

@@ -292,6 +292,7 @@ __global__ void weights_check_kernel(const void *w, int64_t nv, int frac_bits, i
 
 __global__ void max_abs_f64_kernel(const double *x, int64_t n, int stride, int offset, unsigned long long *Mbits)
 {
+    __shared__ unsigned long long wmax[32];
     unsigned long long m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double a = fabs(x[i * stride + offset]);
@@ -302,7 +303,13 @@ __global__ void max_abs_f64_kernel(const double *x, int64_t n, int stride, int o
         const unsigned long long o = __shfl_down_sync(0xffffffffu, m, off);
         m = o > m ? o : m;
     }
-    if ((threadIdx.x & 31) == 0) atomicMax(Mbits, m);
+    // one atomic per block (a per-warp atomic on a single address serialises in L2)
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+        if (m) atomicMax(Mbits, m);
+    }
 }
 
 // Upstream float64 gradient -> int64 table with the largest power-of-two scale 2^k that keeps
@@ -321,6 +328,8 @@ __global__ void grad_quantize_kernel(const double *G, int64_t n, const unsigned 
         k = max(min(k, 1000), -1000);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *scale = ldexp(1.0, -k);
+    // x * 2^k with 2^k an exact double (|k| <= 1000): the same value as ldexp(x, k), one multiply
+    const double p2k = ldexp(1.0, k);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double x = G[i];
         if (!isfinite(x)) {
@@ -328,7 +337,7 @@ __global__ void grad_quantize_kernel(const double *G, int64_t n, const unsigned 
             out[i] = 0;
             continue;
         }
-        out[i] = (m > 0.0) ? __double2ll_rn(ldexp(x, k)) : 0ll;
+        out[i] = (m > 0.0) ? __double2ll_rn(__dmul_rn(x, p2k)) : 0ll;
     }
 }
 

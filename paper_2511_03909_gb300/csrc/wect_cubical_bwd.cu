@@ -156,11 +156,7 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
     int *slotk = reinterpret_cast<int *>(smem + lay.slotk);
     uint8_t *flags = smem + lay.flags;
     const uint32_t ssAddr = smem_addr(Ss), tabAddr = smem_addr(smem + lay.tab);
-    const WorkItem W = P.items[blockIdx.x];
-    const GridDesc g = P.grids[W.cx];
-    const int L0 = g.L[0], L1 = g.L[1];
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
-    const long long *S = reinterpret_cast<const long long *>(P.S) + ((int64_t)W.cx * P.d_all + P.p0) * T;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
 
     if (tid == 0) {
@@ -171,17 +167,6 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
         }
         sb[NOCT] = s;
     }
-    for (int idx = tid; idx < (d + 1) * T; idx += blockDim.x) {
-        const int k = idx / T, q = idx - k * T;
-        Ss[idx] = (k < d) ? S[(int64_t)P.perm[k] * T + q] : 0ll;
-    }
-    for (int k = tid; k < d; k += blockDim.x) {
-        const int p = P.perm[k];
-        double sv[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-        for (int a = 0; a < N; ++a) sv[a] = P.dirs[(int64_t)p * N + a];
-        dfil[k] = make_dir_filter<N>(sv, g.L, lo, hi, step, T);
-    }
     __syncthreads();
     for (int j = tid; j < NS; j += blockDim.x) {
         int k = -1;
@@ -189,113 +174,138 @@ __global__ void __launch_bounds__(1024, 1) cubical_bwd_rsum_kernel(const Cubical
             if (j >= sb[o] && j < sb[o + 1] && P.octb[o] + (j - sb[o]) < P.octb[o + 1]) k = P.octb[o] + (j - sb[o]);
         slotk[j] = k;
     }
-    const int segs = (L0 + 63) >> 6;
     const uint32_t zeroW = ssAddr + 8u * (uint32_t)(d * T) - 8u * (uint32_t)kMagicBits;
-    const RsumCtx C{ssAddr, slotk, dfil, g.L, T, d};
-    for (int rt = W.r0; rt < W.r1; rt += RB) {
-        const int nrt = min(RB, W.r1 - rt);
-        __syncthreads();
-        // filter table of the row tile: one warp per row, lanes over slots
-        for (int rl = wid; rl < nrt; rl += nwarps) {
-            const int r = rt + rl, i1 = r % L1, i2 = r / L1;
-            for (int j0 = 0; j0 < NS; j0 += 32) {
-                const int j = j0 + lane;
-                const int k = (j < NS) ? slotk[j] : -1;
-                float S0 = 0.f, Glo = 0.f, Ghi = 0.f;
-                uint32_t Wj = zeroW;
-                unsigned cf = 0;
-                if (k >= 0) {
-                    const DirFilter f = dfil[k];
-                    const RowFilter rf = make_row_filter<N>(f, i1, i2, g.L);
-                    // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
-                    const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
-                    const float lowf = __fadd_rd(__fsub_rd(rf.Glo, A), (float)(rf.nr - 1));
-                    const float highf = __fadd_ru(__fadd_ru(rf.Ghi, A), (float)(rf.nr + 1));
-                    cf = (!(lowf >= 0.0f) || !(highf <= (float)(T - 1))) ? 1u : 0u;
-                    S0 = f.S0;
-                    Glo = rf.Glo;
-                    Ghi = rf.Ghi;
-                    Wj = ssAddr + 8u * (uint32_t)(k * T + rf.nr) - 8u * (uint32_t)kMagicBits;
-                }
-                cf |= __shfl_xor_sync(0xffffffffu, cf, 1);
-                cf |= __shfl_xor_sync(0xffffffffu, cf, 2);
-                if (j < NS) {
-                    float *e = reinterpret_cast<float *>(smem + lay.tab + ((size_t)rl * NS + (j & ~1)) * 16u);
-                    const int h = j & 1;
-                    e[h] = S0;
-                    e[2 + h] = Glo;
-                    e[4 + h] = Ghi;
-                    reinterpret_cast<uint32_t *>(e)[6 + h] = Wj;
-                    if ((j & (G - 1)) == 0) flags[rl * NG + j / G] = (uint8_t)cf;
-                }
+    const int it0 = P.item_ranges ? P.item_ranges[blockIdx.x] : (int)blockIdx.x;
+    const int it1 = P.item_ranges ? P.item_ranges[blockIdx.x + 1] : (int)blockIdx.x + 1;
+    int staged = -1;                        // complex whose suffix rows and filters are staged
+    for (int item = it0; item < it1; ++item) {
+        const WorkItem W = P.items[item];
+        const GridDesc g = P.grids[W.cx];
+        const int L0 = g.L[0], L1 = g.L[1];
+        if (W.cx != staged) {
+            // the suffix rows of this complex (octant order; row d zero) and its direction filters
+            __syncthreads();                    // the previous complex's readers are done
+            const long long *S = reinterpret_cast<const long long *>(P.S) + ((int64_t)W.cx * P.d_all + P.p0) * T;
+            for (int idx = tid; idx < (d + 1) * T; idx += blockDim.x) {
+                const int k = idx / T, q = idx - k * T;
+                Ss[idx] = (k < d) ? S[(int64_t)P.perm[k] * T + q] : 0ll;
             }
-        }
-        __syncthreads();
-        for (int job = wid; job < nrt * segs; job += nwarps) {
-            const int rl = job / segs, seg = job - rl * segs;
-            // two vertices per lane, 32 apart in the row
-            const int ia = min(seg * 64 + lane, L0 - 1), ib = min(seg * 64 + 32 + lane, L0 - 1);
-            const bool liveA = seg * 64 + lane < L0, liveB = seg * 64 + 32 + lane < L0;
-            const int r = rt + rl, i1 = r % L1, i2 = r / L1;
-            const float ka = (float)(2 * ia - (L0 - 1)), kb = (float)(2 * ib - (L0 - 1));
-            const F2 KA = f2_pack(ka, ka), KB = f2_pack(kb, kb), M2 = f2_pack(kMagic, kMagic);
-            const uint32_t rowTab = tabAddr + (uint32_t)(rl * NS) * 16u;
-            const uint8_t *rowFlags = flags + rl * NG;
-            const int64_t voutA = g.v_off + (int64_t)ia + (int64_t)L0 * r;
-#pragma unroll 1
-            for (int o = 0; o < NOCT; ++o) {
-                long long accA = 0, accB = 0;
-                const int g0 = sb[o] / G, g1 = sb[o + 1] / G;
-                int badOct = 0;
-                // fast pass: no vote and no flag load on the critical path (the next group's
-                // clamp flag is fetched one group ahead)
-                uint8_t fnext = rowFlags[g0];
-#pragma unroll 1
-                for (int gi = g0; gi < g1; ++gi) {
-                    const bool clampg = fnext != 0;
-                    fnext = rowFlags[gi + 1];
-                    uint32_t adA[G], adB[G];
-                    badOct |= rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, clampg, KA, KB, M2, C, i1, i2, adA,
-                                            adB, nullptr, nullptr, nullptr, nullptr);
+            for (int k = tid; k < d; k += blockDim.x) {
+                const int p = P.perm[k];
+                double sv[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        accA += lds_s64(adA[u]);
-                        accB += lds_s64(adB[u]);
+                for (int a = 0; a < N; ++a) sv[a] = P.dirs[(int64_t)p * N + a];
+                dfil[k] = make_dir_filter<N>(sv, g.L, lo, hi, step, T);
+            }
+            staged = W.cx;
+        }
+        const int segs = (L0 + 63) >> 6;
+        const RsumCtx C{ssAddr, slotk, dfil, g.L, T, d};
+        for (int rt = W.r0; rt < W.r1; rt += RB) {
+            const int nrt = min(RB, W.r1 - rt);
+            __syncthreads();
+            // filter table of the row tile: one warp per row, lanes over slots
+            for (int rl = wid; rl < nrt; rl += nwarps) {
+                const int r = rt + rl, i1 = r % L1, i2 = r / L1;
+                for (int j0 = 0; j0 < NS; j0 += 32) {
+                    const int j = j0 + lane;
+                    const int k = (j < NS) ? slotk[j] : -1;
+                    float S0 = 0.f, Glo = 0.f, Ghi = 0.f;
+                    uint32_t Wj = zeroW;
+                    unsigned cf = 0;
+                    if (k >= 0) {
+                        const DirFilter f = dfil[k];
+                        const RowFilter rf = make_row_filter<N>(f, i1, i2, g.L);
+                        // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
+                        const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
+                        const float lowf = __fadd_rd(__fsub_rd(rf.Glo, A), (float)(rf.nr - 1));
+                        const float highf = __fadd_ru(__fadd_ru(rf.Ghi, A), (float)(rf.nr + 1));
+                        cf = (!(lowf >= 0.0f) || !(highf <= (float)(T - 1))) ? 1u : 0u;
+                        S0 = f.S0;
+                        Glo = rf.Glo;
+                        Ghi = rf.Ghi;
+                        Wj = ssAddr + 8u * (uint32_t)(k * T + rf.nr) - 8u * (uint32_t)kMagicBits;
+                    }
+                    cf |= __shfl_xor_sync(0xffffffffu, cf, 1);
+                    cf |= __shfl_xor_sync(0xffffffffu, cf, 2);
+                    if (j < NS) {
+                        float *e = reinterpret_cast<float *>(smem + lay.tab + ((size_t)rl * NS + (j & ~1)) * 16u);
+                        const int h = j & 1;
+                        e[h] = S0;
+                        e[2 + h] = Glo;
+                        e[4 + h] = Ghi;
+                        reinterpret_cast<uint32_t *>(e)[6 + h] = Wj;
+                        if ((j & (G - 1)) == 0) flags[rl * NG + j / G] = (uint8_t)cf;
                     }
                 }
-                if (__any_sync(0xffffffffu, badOct != 0)) {
-                    // undecided bins somewhere in this octant: replace their candidate entries
-                    // by the entries of the exact float64 bins
+            }
+            __syncthreads();
+            for (int job = wid; job < nrt * segs; job += nwarps) {
+                const int rl = job / segs, seg = job - rl * segs;
+                // two vertices per lane, 32 apart in the row
+                const int ia = min(seg * 64 + lane, L0 - 1), ib = min(seg * 64 + 32 + lane, L0 - 1);
+                const bool liveA = seg * 64 + lane < L0, liveB = seg * 64 + 32 + lane < L0;
+                const int r = rt + rl, i1 = r % L1, i2 = r / L1;
+                const float ka = (float)(2 * ia - (L0 - 1)), kb = (float)(2 * ib - (L0 - 1));
+                const F2 KA = f2_pack(ka, ka), KB = f2_pack(kb, kb), M2 = f2_pack(kMagic, kMagic);
+                const uint32_t rowTab = tabAddr + (uint32_t)(rl * NS) * 16u;
+                const uint8_t *rowFlags = flags + rl * NG;
+                const int64_t voutA = g.v_off + (int64_t)ia + (int64_t)L0 * r;
+#pragma unroll 1
+                for (int o = 0; o < NOCT; ++o) {
+                    long long accA = 0, accB = 0;
+                    const int g0 = sb[o] / G, g1 = sb[o + 1] / G;
+                    int badOct = 0;
+                    // fast pass: no vote and no flag load on the critical path (the next group's
+                    // clamp flag is fetched one group ahead)
+                    uint8_t fnext = rowFlags[g0];
 #pragma unroll 1
                     for (int gi = g0; gi < g1; ++gi) {
+                        const bool clampg = fnext != 0;
+                        fnext = rowFlags[gi + 1];
                         uint32_t adA[G], adB[G];
-                        int tA[G], hA[G], tB[G], hB[G];
-                        if (!rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, rowFlags[gi] != 0, KA, KB, M2, C, i1,
-                                           i2, adA, adB, tA, hA, tB, hB))
-                            continue;
+                        badOct |= rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, clampg, KA, KB, M2, C, i1, i2, adA,
+                                                adB, nullptr, nullptr, nullptr, nullptr);
 #pragma unroll
                         for (int u = 0; u < G; ++u) {
-                            const int k = slotk[gi * G + u];
-                            if (k < 0) continue;
-                            const double *sp = P.dirs + (int64_t)P.perm[k] * N;
-                            if (tA[u] != hA[u]) {
-                                const int cand = (int)((adA[u] - ssAddr) >> 3) - k * T;
-                                const double h = height3<N>(gcoord(g, 0, ia), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
-                                accA += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adA[u]);
-                            }
-                            if (tB[u] != hB[u]) {
-                                const int cand = (int)((adB[u] - ssAddr) >> 3) - k * T;
-                                const double h = height3<N>(gcoord(g, 0, ib), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
-                                accB += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adB[u]);
+                            accA += lds_s64(adA[u]);
+                            accB += lds_s64(adB[u]);
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, badOct != 0)) {
+                        // undecided bins somewhere in this octant: replace their candidate entries
+                        // by the entries of the exact float64 bins
+#pragma unroll 1
+                        for (int gi = g0; gi < g1; ++gi) {
+                            uint32_t adA[G], adB[G];
+                            int tA[G], hA[G], tB[G], hB[G];
+                            if (!rsum_group<N>(rowTab + (uint32_t)gi * (G * 16u), gi, rowFlags[gi] != 0, KA, KB, M2, C, i1,
+                                               i2, adA, adB, tA, hA, tB, hB))
+                                continue;
+#pragma unroll
+                            for (int u = 0; u < G; ++u) {
+                                const int k = slotk[gi * G + u];
+                                if (k < 0) continue;
+                                const double *sp = P.dirs + (int64_t)P.perm[k] * N;
+                                if (tA[u] != hA[u]) {
+                                    const int cand = (int)((adA[u] - ssAddr) >> 3) - k * T;
+                                    const double h = height3<N>(gcoord(g, 0, ia), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
+                                    accA += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adA[u]);
+                                }
+                                if (tB[u] != hB[u]) {
+                                    const int cand = (int)((adB[u] - ssAddr) >> 3) - k * T;
+                                    const double h = height3<N>(gcoord(g, 0, ib), gcoord(g, 1, i1), gcoord(g, 2, i2), sp);
+                                    accB += Ss[k * T + exact_bin_from(h, P.beta, T, cand)] - lds_s64(adB[u]);
+                                }
                             }
                         }
                     }
+                    if (liveA) store_split(P.Rv + (int64_t)o * P.total_nv + voutA, accA, P.accumulate != 0);
+                    if (liveB) store_split(P.Rv + (int64_t)o * P.total_nv + voutA + 32, accB, P.accumulate != 0);
                 }
-                if (liveA) store_split(P.Rv + (int64_t)o * P.total_nv + voutA, accA, P.accumulate != 0);
-                if (liveB) store_split(P.Rv + (int64_t)o * P.total_nv + voutA + 32, accB, P.accumulate != 0);
             }
         }
-    }
+    }   // items of this CTA
 }
 
 // Route each cell's gradient to its heaviest vertex:

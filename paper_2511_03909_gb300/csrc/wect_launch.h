@@ -53,6 +53,9 @@ struct CubicalBwdArgs {
     // perm and octb describe the chunk, whose rows start at direction p0 of the d_all rows of S;
     // accumulate adds the chunk's sums to Rv instead of storing them
     int d_all, p0, accumulate;
+    // CTA b of the octant sums takes items [item_ranges[b], item_ranges[b + 1]) in order (a
+    // balanced contiguous share of all rows), or item b alone when null
+    const int *item_ranges;
 };
 
 struct SimplexFwdArgs {
