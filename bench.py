@@ -561,7 +561,8 @@ def secondary(P, S, dev, steps, flush, local):
 
 def run_case(name):
     """Run one small workload a few times, untimed, for ncu captures of kernels the headline
-    step does not launch (the adjoint, the simplicial gather, the batch, the ECF)."""
+    step does not launch (the adjoint, the run-based stencil, the simplicial gather, the batch,
+    the ECF)."""
     import torch
 
     sys.path.insert(0, ROOT)
@@ -580,6 +581,21 @@ def run_case(name):
             g = bb.backward(dirs, wv.T, wv.lo, wv.hi, D, 2.0 ** -23 / D.numel())
         torch.cuda.synchronize()
         print("adjoint16 ok", float(g.abs().sum()))
+    elif name == "run128":
+        # the 128^3 u8 volume, d = 256 Fibonacci, T = 128, through the run-based stencil kernel
+        # (forced with the kernel-selection hook): three calls
+        wl = S.voxel3d_128()
+        cx = P.CubicalComplex(torch.from_numpy(wl.grid).to(dev))
+        dirs = torch.from_numpy(wl.dirs).to(dev)
+        P.stencil_variant(2)
+        try:
+            for _ in range(3):
+                W = cx.wect(dirs, wl.T, wl.lo, wl.hi)
+            torch.cuda.synchronize()
+            kernel = P.last_stencil_kernel()
+        finally:
+            P.stencil_variant(0)
+        print("run128 ok", kernel, int(W[:, -1].sum()))
     elif name == "mesh64":
         # the 1024^2 mesh with d = 64 directions (two 32-direction tiles), T = 512, range [-1.5, 1.5]
         wl = S.mesh2d_1024(d=64)
@@ -637,7 +653,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the batched-vs-loop, forward+backward and ECF sections")
-    ap.add_argument("--case", choices=["adjoint16", "mesh64", "batch4096", "ecf4096", "wecf64"],
+    ap.add_argument("--case", choices=["adjoint16", "run128", "mesh64", "batch4096", "ecf4096", "wecf64"],
                     help="run one untimed workload for an ncu capture (no JSON line)")
     args = ap.parse_args()
     if args.case:

@@ -220,6 +220,21 @@ WECT_API wect_status wecf_compute(wect_complex cx, const double *filters, int m,
 WECT_API wect_status wect_backward(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
                           const int64_t *dW, double scale, float *grad_w, wect_stream stream);
 
+/*
+ * Adjoint of wect_compute for a float64 upstream gradient G = dL/dW (dev [d][T]) with W in real
+ * units (the fixed-point table times 2^-frac_bits), so grad_w[v] = dL/dw_v for the real-valued
+ * vertex weights (the vertex-weight gradient of Section 3's differentiable transform; the
+ * autograd function of the Python binding calls this).  G is quantised on the device to int64
+ * with the largest power-of-two scale 2^k that keeps H * max|G| * 2^k below 2^62, H = d * T on
+ * a simplicial complex and 3^n * d * T on a grid (each rounded up to a power of two): exact
+ * when G's values are multiples of 2^-k.  The rest is wect_backward with scale 2^-k.
+ * Asynchronous: no host synchronisation.  A non-finite entry of G counts as zero and flags
+ * the device status word, which wect_complex_device_status then reports as
+ * WECT_ERR_INVALID_ARG.  Errors: as wect_backward.
+ */
+WECT_API wect_status wect_backward_f64(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
+                                       const double *G, float *grad_w, wect_stream stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /*
@@ -380,6 +395,8 @@ WECT_API wect_status wect_debug_fail_alloc(int64_t k);
  *               thresholds per row
  *   variant 1   the per-vertex kernel only
  *   variant 2   the run kernel wherever it applies
+ *   variant 3   the per-vertex kernel, reading the neighbouring rows from global memory
+ *               instead of staging them in shared memory by TMA
  * Process-wide; affects compute calls made afterwards (a batch's tuned shape takes precedence,
  * and graphs already captured keep their kernel).  INVALID_ARG for another value.
  */

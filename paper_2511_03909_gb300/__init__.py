@@ -7,8 +7,9 @@ raises.
 
 Low-level functions carry the C names (``wect_complex_create_cubical``, ``wect_compute``,
 ``ecf_compute``, ``wect_backward``, ``wect_batch_*``).  The classes ``CubicalComplex``,
-``SimplicialComplex`` and ``CubicalBatch`` wrap the handles, and ``WECTFunction`` is the
-``torch.autograd.Function`` whose backward is the library's exact adjoint.
+``SimplicialComplex`` and ``CubicalBatch`` wrap the handles; ``WECTFunction`` (batches of
+grids) and ``ComplexWECTFunction`` (one grid or simplicial complex) are the
+``torch.autograd.Function`` classes whose backward is the library's exact adjoint.
 """
 from __future__ import annotations
 
@@ -22,7 +23,7 @@ from ._build import LIB as _LIB_PATH
 
 __all__ = [
     "WectError", "load", "CubicalComplex", "FreudenthalComplex", "SimplicialComplex", "CubicalBatch", "WECTFunction",
-    "wect", "ecf", "launch_count", "library_path",
+    "ComplexWECTFunction",     "wect", "ecf", "launch_count", "library_path",
 ]
 
 W_U8, W_I64_FIXED, W_F32, W_ONE = 0, 1, 2, 3
@@ -78,6 +79,7 @@ def _declare(L):
         "ecf_compute": (_st, [_p, _p, _i, _d, _d, _i, _p, _p]),
         "wecf_compute": (_st, [_p, _p, _i, _i, _d, _d, _i, _p, _p]),
         "wect_backward": (_st, [_p, _p, _i, _i, _d, _d, _p, _d, _p, _p]),
+        "wect_backward_f64": (_st, [_p, _p, _i, _i, _d, _d, _p, _p, _p]),
         "wect_batch_create": (_st, [_i, _p, _p]),
         "wect_batch_create_cubical": (_st, [_i, _i, _p, _p, _i, _i, _p, _p]),
         "wect_batch_set_weights": (_st, [_p, _p, _p]),
@@ -113,7 +115,8 @@ def exported_symbols():
         "wect_complex_create_cubical", "wect_complex_create_freudenthal", "wect_complex_create_simplicial",
         "wect_complex_set_weights",
         "wect_complex_num_vertices", "wect_complex_cell_counts", "wect_complex_device_status",
-        "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_batch_create",
+        "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_backward_f64",
+        "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
         "wect_batch_autotune", "wect_batch_tuned_shape",
@@ -182,7 +185,8 @@ def debug_fail_alloc(k: int):
 
 def stencil_variant(variant: int):
     """wect_debug_stencil_variant: 0 = choose the cubical stencil kernel by cost, 1 = the
-    per-vertex kernel only, 2 = the run-based kernel wherever it applies."""
+    per-vertex kernel only, 2 = the run-based kernel wherever it applies, 3 = the per-vertex
+    kernel without the TMA staging of the neighbouring rows."""
     _check(load().wect_debug_stencil_variant(int(variant)))
 
 
@@ -197,6 +201,7 @@ class _Complex:
     _h = None
     n = 0
     nv = 0
+    frac_bits = 0
 
     def __del__(self):
         if self._h is not None and _lib is not None:
@@ -270,6 +275,18 @@ class _Complex:
                                     _stream()))
         return grad
 
+    def backward_f64(self, dirs: torch.Tensor, T: int, lo: float, hi: float, G: torch.Tensor,
+                     grad: torch.Tensor | None = None) -> torch.Tensor:
+        """Adjoint for a float64 upstream gradient in real units (wect_backward_f64)."""
+        _require_cuda(dirs, "dirs", torch.float64)
+        _require_cuda(G, "G", torch.float64)
+        if G.shape != (dirs.shape[0], T):
+            raise ValueError("G must be [d][T]")
+        if grad is None:
+            grad = torch.empty(self.nv, dtype=torch.float32, device=dirs.device)
+        _check(load().wect_backward_f64(self._h, _ptr(dirs), dirs.shape[0], T, lo, hi, _ptr(G), _ptr(grad), _stream()))
+        return grad
+
 
 class CubicalComplex(_Complex):
     """Full cubical complex of an n-dimensional grid (wect_complex_create_cubical).
@@ -281,6 +298,7 @@ class CubicalComplex(_Complex):
 
     def __init__(self, weights: torch.Tensor | None, frac_bits: int = 0, dims=None):
         L = load()
+        self.frac_bits = int(frac_bits)
         if weights is not None:
             _require_cuda(weights, "weights")
             dims = list(reversed(weights.shape))
@@ -303,6 +321,7 @@ class FreudenthalComplex(_Complex):
 
     def __init__(self, weights: torch.Tensor | None, frac_bits: int = 0, dims=None):
         L = load()
+        self.frac_bits = int(frac_bits)
         if weights is not None:
             _require_cuda(weights, "weights")
             dims = list(reversed(weights.shape))
@@ -329,6 +348,7 @@ class SimplicialComplex(_Complex):
     def __init__(self, coords: torch.Tensor, simplices, weights: torch.Tensor | None = None, frac_bits: int = 0,
                  simplex_weights=None):
         L = load()
+        self.frac_bits = int(frac_bits)
         _require_cuda(coords, "coords", torch.float64)
         self.nv, self.n = int(coords.shape[0]), int(coords.shape[1])
         self.max_dim = len(simplices)
@@ -458,6 +478,30 @@ class WECTFunction(torch.autograd.Function):
     def backward(ctx, gW: torch.Tensor):
         b = ctx.batch
         grad = b.backward_f64(ctx.dirs, ctx.T, ctx.lo, ctx.hi, gW.to(torch.float64).contiguous())
+        return None, grad, None, None, None, None
+
+
+class ComplexWECTFunction(torch.autograd.Function):
+    """W = WECT(vertex weights) of one complex (grid, Freudenthal or simplicial in max-of-vertices
+    mode), with the library's exact adjoint as backward.
+
+    forward(complex, weights, dirs, T, lo, hi) -> float64 [d][T] in real units (the int64
+    fixed-point result * 2^-frac_bits).  ``weights`` are the vertex weights in the form the
+    complex was created with (set on the complex by the forward).  backward passes the float64
+    upstream gradient to wect_backward_f64 (quantised on the device, no host sync) and returns
+    a float32 gradient per vertex.
+    """
+
+    @staticmethod
+    def forward(ctx, cx: _Complex, w: torch.Tensor, dirs: torch.Tensor, T: int, lo: float, hi: float):
+        cx.set_weights(w.detach().contiguous())
+        W = cx.wect(dirs, T, lo, hi)
+        ctx.cx, ctx.dirs, ctx.T, ctx.lo, ctx.hi = cx, dirs, T, lo, hi
+        return W.to(torch.float64) * (2.0 ** -cx.frac_bits)     # exact: a power of two
+
+    @staticmethod
+    def backward(ctx, gW: torch.Tensor):
+        grad = ctx.cx.backward_f64(ctx.dirs, ctx.T, ctx.lo, ctx.hi, gW.to(torch.float64).contiguous())
         return None, grad, None, None, None, None
 
 

@@ -580,6 +580,13 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     return WECT_OK;
 }
 
+static int ceil_log2(int64_t x)
+{
+    int k = 0;
+    while (((int64_t)1 << k) < x) ++k;
+    return k;
+}
+
 static wect_status ensure_common_ws(Workspace &ws, int T, int d = 1)
 {
     CK(ws.perm.ensure((size_t)d), "alloc");
@@ -1263,28 +1270,21 @@ static wect_status cubical_backward(const GridDesc *d_grids, int n_grids, const 
     return WECT_OK;
 }
 
-extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
-                                     const int64_t *dW, double scale, float *grad_w, wect_stream stream)
+// The adjoint of one complex (the caller holds its lock).  grad_w = I_v * scale, or I_v times
+// the device-side scale *scale_dev when that is not null (the quantised float64 upstream).
+static wect_status complex_backward(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                    const int64_t *dW, double scale, const double *scale_dev, float *grad_w,
+                                    cudaStream_t st)
 {
-    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
-    if (!dirs || !dW || !grad_w) return fail(WECT_ERR_INVALID_ARG, "NULL pointer argument");
-    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
-    if (!std::isfinite(scale)) return fail(WECT_ERR_INVALID_ARG, "scale must be finite");
-    wect_status s = check_range(lo, hi, T);
-    if (s) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(c->mu);
-    if ((s = dirs_check(c, dirs, d, st))) return s;
+    wect_status s;
     if (c->kind == 0) {
         std::vector<GridDesc> hg(1);
         hg[0].L[0] = c->L[0]; hg[0].L[1] = c->L[1]; hg[0].L[2] = c->L[2];
         hg[0].rows = c->L[1] * c->L[2];
         hg[0].nv = c->nv;
         return cubical_backward(c->d_grid, 1, hg, c->n, c->wtype, c->frac_bits, c->nv, c->ws, dirs, d, T, lo, hi, dW, scale,
-                                grad_w, c->d_status, st);
+                                grad_w, c->d_status, st, scale_dev);
     }
-    if (c->sw_mode != WECT_SW_MAX_OF_VERTICES)
-        return fail(WECT_ERR_UNSUPPORTED, "the adjoint needs simplex weights that are the max of the vertex weights");
     if ((s = ensure_common_ws(c->ws, T))) return s;
     CK(c->ws.S.ensure((size_t)d * T), "alloc S");
     CK(c->ws.bins.ensure((size_t)c->nv * 32), "alloc bins");
@@ -1293,10 +1293,57 @@ extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, 
     KL(launch_suffix_rows(dW, c->ws.S.p, d, T, INT64_MAX / d, c->d_status, st), "suffix_rows");
     const int32_t *simp[kMaxSimplexDim + 1] = {nullptr, c->d_simp[1], c->d_simp[2], c->d_simp[3], c->d_simp[4]};
     CK(launch_simplicial_bwd(c->n, c->d_coords, c->d_xf, c->nv, simp, c->counts, c->max_dim, c->d_sw[0], dirs, d, T, c->ws.dtab.p,
-                             c->ws.beta.p, c->ws.S.p, c->ws.bins.p, c->ws.Iacc.p, grad_w, scale, st),
+                             c->ws.beta.p, c->ws.S.p, c->ws.bins.p, c->ws.Iacc.p, grad_w, scale, scale_dev, st),
        "simplicial_bwd");
     g_launches += 1 + ((d + 31) / 32) * (1 + c->max_dim + 1);
     return WECT_OK;
+}
+
+static wect_status backward_checks(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                   const void *up, float *grad_w)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    if (!dirs || !up || !grad_w) return fail(WECT_ERR_INVALID_ARG, "NULL pointer argument");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    if (c->kind != 0 && c->sw_mode != WECT_SW_MAX_OF_VERTICES)
+        return fail(WECT_ERR_UNSUPPORTED, "the adjoint needs simplex weights that are the max of the vertex weights");
+    return WECT_OK;
+}
+
+extern "C" wect_status wect_backward(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                     const int64_t *dW, double scale, float *grad_w, wect_stream stream)
+{
+    wect_status s = backward_checks(c, dirs, d, T, lo, hi, dW, grad_w);
+    if (s) return s;
+    if (!std::isfinite(scale)) return fail(WECT_ERR_INVALID_ARG, "scale must be finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if ((s = dirs_check(c, dirs, d, st))) return s;
+    return complex_backward(c, dirs, d, T, lo, hi, dW, scale, nullptr, grad_w, st);
+}
+
+extern "C" wect_status wect_backward_f64(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
+                                         const double *G, float *grad_w, wect_stream stream)
+{
+    wect_status s = backward_checks(c, dirs, d, T, lo, hi, G, grad_w);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if ((s = dirs_check(c, dirs, d, st))) return s;
+    if ((s = ensure_common_ws(c->ws, T, d))) return s;
+    const int64_t n = (int64_t)d * T;
+    CK(c->ws.Gq.ensure((size_t)n), "alloc");
+    CK(c->ws.gscale.ensure(1), "alloc");
+    // headroom: suffix sums over T and sums over d directions, and on a grid the signed sums over
+    // the 3^n cells of a vertex
+    const int head = ceil_log2(T) + ceil_log2(d) +
+                     (c->kind == 0 ? ceil_log2(c->n == 1 ? 3 : (c->n == 2 ? 9 : 27)) : 0);
+    KL(launch_grad_quantize(G, n, head, c->ws.M.p, c->ws.Gq.p, c->ws.gscale.p, c->d_status, st), "grad_quantize");
+    g_launches++;
+    return complex_backward(c, dirs, d, T, lo, hi, reinterpret_cast<const int64_t *>(c->ws.Gq.p), 1.0, c->ws.gscale.p,
+                            grad_w, st);
 }
 
 // ------------------------------------------------------------------ batches
@@ -1672,13 +1719,6 @@ extern "C" wect_status wect_batch_backward(wect_batch b, const double *dirs, int
     std::lock_guard<std::mutex> lk(b->mu);
     return cubical_backward(b->d_grids, b->count, b->h_grids, b->n, b->wtype, b->frac_bits, b->total_nv, b->ws, dirs, d, T,
                             lo, hi, dW, scale, grad_w, b->d_status, st);
-}
-
-static int ceil_log2(int64_t x)
-{
-    int k = 0;
-    while (((int64_t)1 << k) < x) ++k;
-    return k;
 }
 
 extern "C" wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, int d, int T, double lo, double hi,

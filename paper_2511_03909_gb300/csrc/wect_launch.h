@@ -164,7 +164,7 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
                                   const int64_t *counts, int max_dim, const int64_t *vw, const double *dirs, int d,
                                   int T, const float *tab, const double *beta, const int64_t *S,
                                   uint16_t *bins, unsigned long long *Iacc, float *grad, double scale,
-                                  cudaStream_t st);
+                                  const double *scale_dev, cudaStream_t st);
 cudaError_t launch_simplex_ecf(const int32_t *simp, const int64_t *sw, int64_t k, int m, int sign, int weighted,
                                int64_t wbound, const uint16_t *bins, int T, unsigned long long *out, int64_t nv,
                                int nf, cudaStream_t st);

@@ -778,10 +778,13 @@ __global__ void simplex_bwd_kernel(const int32_t *simp, int64_t k, int sign, con
     }
 }
 
-__global__ void i128_to_grad_kernel(const unsigned long long *Iacc, int64_t nv, double scale, float *grad)
+// grad[v] = I_v * scale, with the scale from device memory when scale_dev is not null.
+__global__ void i128_to_grad_kernel(const unsigned long long *Iacc, int64_t nv, double scale, const double *scale_dev,
+                                    float *grad)
 {
+    const double sc = scale_dev ? *scale_dev : scale;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x)
-        grad[v] = (float)(i128_to_double((int64_t)Iacc[2 * v + 1], Iacc[2 * v]) * scale);
+        grad[v] = (float)(i128_to_double((int64_t)Iacc[2 * v + 1], Iacc[2 * v]) * sc);
 }
 
 // WECF scatter of one list of M-vertex simplices for caller filters (Algorithm 1 with the vertex
@@ -1005,7 +1008,7 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
                                   const int64_t *counts, int max_dim, const int64_t *vw, const double *dirs, int d,
                                   int T, const float *tab, const double *beta, const int64_t *S,
                                   uint16_t *bins, unsigned long long *Iacc, float *grad, double scale,
-                                  cudaStream_t st)
+                                  const double *scale_dev, cudaStream_t st)
 {
     const int Dt = 32;
     cudaError_t e = cudaMemsetAsync(Iacc, 0, (size_t)nv * 16u, st);
@@ -1027,7 +1030,8 @@ cudaError_t launch_simplicial_bwd(int n, const double *coords, const float *xf, 
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    i128_to_grad_kernel<<<(unsigned)std::min<int64_t>((nv + 255) / 256, 4096), 256, 0, st>>>(Iacc, nv, scale, grad);
+    i128_to_grad_kernel<<<(unsigned)std::min<int64_t>((nv + 255) / 256, 4096), 256, 0, st>>>(Iacc, nv, scale, scale_dev,
+                                                                                                 grad);
     return cudaGetLastError();
 }
 
