@@ -489,20 +489,20 @@ class ComplexWECTFunction(torch.autograd.Function):
     fixed-point result * 2^-frac_bits).  ``weights`` are the vertex weights in the form the
     complex was created with (set on the complex by the forward).  backward passes the float64
     upstream gradient to wect_backward_f64 (quantised on the device, no host sync) and returns
-    a float32 gradient per vertex.
+    a float32 gradient per vertex, in the shape of ``weights``.
     """
 
     @staticmethod
     def forward(ctx, cx: _Complex, w: torch.Tensor, dirs: torch.Tensor, T: int, lo: float, hi: float):
         cx.set_weights(w.detach().contiguous())
         W = cx.wect(dirs, T, lo, hi)
-        ctx.cx, ctx.dirs, ctx.T, ctx.lo, ctx.hi = cx, dirs, T, lo, hi
+        ctx.cx, ctx.dirs, ctx.T, ctx.lo, ctx.hi, ctx.wshape = cx, dirs, T, lo, hi, w.shape
         return W.to(torch.float64) * (2.0 ** -cx.frac_bits)     # exact: a power of two
 
     @staticmethod
     def backward(ctx, gW: torch.Tensor):
         grad = ctx.cx.backward_f64(ctx.dirs, ctx.T, ctx.lo, ctx.hi, gW.to(torch.float64).contiguous())
-        return None, grad, None, None, None, None
+        return None, grad.view(ctx.wshape), None, None, None, None
 
 
 # ------------------------------------------------------------------ allocation-free variant

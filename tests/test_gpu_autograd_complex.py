@@ -106,7 +106,8 @@ def test_backward_f64_default_range_and_nonfinite_upstream(P, oracle):
     G = np.random.default_rng(37).integers(-64, 64, (len(dirs), T)).astype(np.float64) * 2.0 ** -10
     g = h.backward_f64(cuda(dirs), T, math.nan, math.nan, cuda(G)).cpu().numpy()
     vw = oracle.fixed_from_f32(cx.weights, 24)
-    ref = oracle.wect_backward_simplicial(cx.coords, vw, cx.simplices, dirs, T, math.nan, math.nan,
+    lo, hi = oracle.default_range_simplicial(cx.coords, dirs)
+    ref = oracle.wect_backward_simplicial(cx.coords, vw, cx.simplices, dirs, T, lo, hi,
                                           (G * 2.0 ** 10).astype(np.int64), 2.0 ** -10)
     assert np.array_equal(g, ref)
     h.device_status()
