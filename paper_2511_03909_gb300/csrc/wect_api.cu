@@ -856,11 +856,22 @@ extern "C" wect_status wect_complex_create_simplicial(int n, int64_t n_vertices,
         const int64_t hb = (c->climit >> 16) + 1;
         c->kflush = (int)std::max<int64_t>(1, std::min<int64_t>(1 << 16, (((int64_t)1 << 31) - 1) / hb));
     }
-    // lists sorted by smallest vertex (results do not depend on the order; the gather's chunks
-    // then reference few distinct vertices)
-    for (int i = 1; i <= max_dim; ++i)
-        if (counts[i] > 1 && (e = sort_simplices_by_min_vertex(c->d_simp[i], counts[i], i + 1, c->d_sw[i], n_vertices, st)))
-            return cleanup(cuda_fail(e, "sort lists"));
+    // lists sorted by a spatial key (results do not depend on the order; the gather's chunks then
+    // cover compact patches and reference few distinct vertices)
+    bool any_list = false;
+    for (int i = 1; i <= max_dim; ++i) any_list |= counts[i] > 1;
+    if (any_list) {
+        unsigned long long *vkey = nullptr;
+        if ((e = dev_malloc((void **)&vkey, (size_t)n_vertices * sizeof(unsigned long long))))
+            return cleanup(cuda_fail(e, "alloc sort keys"));
+        e = vertex_morton_keys(c->d_coords, n_vertices, n, xm, vkey, st);
+        g_launches++;
+        for (int i = 1; i <= max_dim && e == cudaSuccess; ++i)
+            if (counts[i] > 1) e = sort_simplices_spatial(c->d_simp[i], counts[i], i + 1, c->d_sw[i], vkey, st);
+        cudaStreamSynchronize(st);
+        cudaFree(vkey);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "sort lists"));
+    }
     for (int i = 0; i <= max_dim; ++i)
         if ((e = dev_malloc((void **)&c->d_swp[i], std::max<int64_t>(counts[i], 1) * sizeof(int2))))
             return cleanup(cuda_fail(e, "alloc packed weights"));

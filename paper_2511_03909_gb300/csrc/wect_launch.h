@@ -145,7 +145,12 @@ cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, co
 cudaError_t launch_pack_weights(const int64_t *sw, int64_t k, int sign, int nsplit, int2 *out, cudaStream_t st);
 // Stable sort of a list of k simplices (m vertices each, in place) by smallest vertex id; sw (may
 // be null) is permuted alike.  Creation time only: it allocates and synchronises the stream.
-cudaError_t sort_simplices_by_min_vertex(int32_t *simp, int64_t k, int m, int64_t *sw, int64_t nv, cudaStream_t st);
+// Morton code of every vertex (coordinates [nv][n], quantised on the box [-xm_a, xm_a]) and the
+// stable sort of a list by the smallest code among each simplex's vertices.
+cudaError_t vertex_morton_keys(const double *coords, int64_t nv, int n, const double *xm, unsigned long long *vkey,
+                               cudaStream_t st);
+cudaError_t sort_simplices_spatial(int32_t *simp, int64_t k, int m, int64_t *sw, const unsigned long long *vkey,
+                                   cudaStream_t st);
 // Chunk-local ids of a list of k simplices with m vertices (m >= 2): per chunk its distinct vertices
 // (cverts, cnu) and the list rewritten in chunk-local 16-bit ids (local).
 cudaError_t launch_chunk_local(const int32_t *simp, int64_t k, int m, uint16_t *local, int32_t *cverts, int32_t *cnu,
