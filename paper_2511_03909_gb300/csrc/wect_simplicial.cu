@@ -203,6 +203,78 @@ __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vb
     }
 }
 
+__device__ __forceinline__ int lds_u16(uint32_t addr)
+{
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return (int)v;
+}
+
+__device__ __forceinline__ int2 lds_v2s32(uint32_t addr)
+{
+    int2 v;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+// gather_group for a staged chunk, every operand addressed in the shared window directly (32-bit
+// shared addresses): ids is the address of the group's M * GS window-row offsets (u16 byte
+// offsets), wts of its GS packed weights, winLane the window's address plus 2 * lane.
+template <int NSPLIT, int M, int GS>
+__device__ __forceinline__ void gather_group_staged(uint32_t ids, uint32_t wts, int n, uint32_t winLane,
+                                                    uint32_t histLane, uint32_t HOFF)
+{
+    int off[GS][M];
+    int2 w[GS];
+    if (n == GS) {
+        static_assert(GS == 8, "vector loads assume groups of 8");
+        uint32_t word[GS * M / 2];
+#pragma unroll
+        for (int q = 0; q < GS * M / 8; ++q) {
+            const int4 x = lds128(ids + 16u * q);
+            word[4 * q] = (uint32_t)x.x;
+            word[4 * q + 1] = (uint32_t)x.y;
+            word[4 * q + 2] = (uint32_t)x.z;
+            word[4 * q + 3] = (uint32_t)x.w;
+        }
+#pragma unroll
+        for (int g = 0; g < GS; ++g)
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const int e = g * M + j;
+                off[g][j] = (int)((word[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+            }
+#pragma unroll
+        for (int q = 0; q < GS / 2; ++q) {
+            const int4 x = lds128(wts + 16u * q);
+            w[2 * q] = make_int2(x.x, x.y);
+            w[2 * q + 1] = make_int2(x.z, x.w);
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < GS; ++g) {
+            const int gi = min(g, n - 1);
+#pragma unroll
+            for (int j = 0; j < M; ++j) off[g][j] = lds_u16(ids + 2u * (uint32_t)(gi * M + j));
+            w[g] = (g < n) ? lds_v2s32(wts + 8u * (uint32_t)gi) : make_int2(0, 0);
+        }
+    }
+    int bin[GS];
+#pragma unroll
+    for (int g = 0; g < GS; ++g) {
+        int bm = 0;
+#pragma unroll
+        for (int j = 0; j < M; ++j) bm = max(bm, lds_u16(winLane + (uint32_t)off[g][j]));
+        bin[g] = bm;
+    }
+#pragma unroll
+    for (int g = 0; g < GS; ++g) {
+        const uint32_t addr = histLane + (uint32_t)bin[g] * 128u;
+        red_shared_add(addr, w[g].x);
+        if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
+    }
+}
+
 // Add a CTA's [NSPLIT][T][32] int32 histogram (low 16 bits unsigned + high part when NSPLIT = 2)
 // into the int64 [d][T] difference table of the tile's directions, and clear it.
 template <int NSPLIT>
@@ -314,8 +386,35 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     // coordinates and weights of the warp's next group, loaded one step ahead
     float xn[VG][N];
     int2 wn[VG];
+    static_assert(VG % 2 == 0 && (VG * N) % 4 == 0, "128-bit group loads");
     auto load_group = [&](int64_t base) {
         const int v0 = (int)(base + (int64_t)wid * VG);
+        if (v0 <= nvm1 - (VG - 1)) {
+            // a whole group: its coordinates and packed weights are contiguous and 16-byte
+            // aligned (v0 is a multiple of VG), so 128-bit loads
+            const float4 *xs = reinterpret_cast<const float4 *>(xf + (int64_t)v0 * N);
+            float xv[VG * N];
+#pragma unroll
+            for (int q = 0; q < VG * N / 4; ++q) {
+                const float4 t = __ldg(xs + q);
+                xv[4 * q] = t.x;
+                xv[4 * q + 1] = t.y;
+                xv[4 * q + 2] = t.z;
+                xv[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int g = 0; g < VG; ++g)
+#pragma unroll
+                for (int a = 0; a < N; ++a) xn[g][a] = xv[g * N + a];
+            const int4 *ws = reinterpret_cast<const int4 *>(P.swp + v0);
+#pragma unroll
+            for (int q = 0; q < VG / 2; ++q) {
+                const int4 t = __ldg(ws + q);
+                wn[2 * q] = make_int2(t.x, t.y);
+                wn[2 * q + 1] = make_int2(t.z, t.w);
+            }
+            return;
+        }
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
             const int v = min(v0 + g, nvm1);
@@ -340,6 +439,7 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
         // branch-free pass: candidate bins, stores and scatters; undecided bins are only marked
         int bc[VG];
         uint32_t pend = 0;
+        uint16_t *brow = bins + (int64_t)v0 * 32 + lane;       // this lane's column of the group's rows
 #pragma unroll
         for (int g = 0; g < VG; ++g) {
             float u = Cf;
@@ -352,7 +452,7 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
             pend |= (tlo != thi ? 1u : 0u) << g;
             // every column gets a valid bin (a padding column carries direction d - 1's), so the
             // gathers never read an unwritten entry
-            if (v0 + g <= nvm1) bins[(int64_t)(v0 + g) * 32 + lane] = (uint16_t)b;
+            if (v0 + g <= nvm1) brow[g * 32] = (uint16_t)b;
             const uint32_t addr = histLane + (uint32_t)b * 128u;
             red_shared_add(addr, w[g].x);
             if (NSPLIT == 2) red_shared_add(addr + HOFF, w[g].y);
@@ -399,7 +499,8 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
 // Creation-time pass over a list of simplices with M >= 2 vertices, one CTA per chunk of
 // chunk_simplices(M) simplices: sort the chunk's vertex ids, keep the distinct ones (thread 0, a
 // serial pass over at most kChunkSlots sorted ids), and when there are at most kWinRows of them
-// store them in cverts and rewrite the chunk's ids as their ranks (16 bits).  cnu is the number
+// store them in cverts and rewrite the chunk's ids as the byte offsets of their rows in the
+// staged window (rank * 64, below kWinRows * 64 = 34816: 16 bits).  cnu is the number
 // of distinct vertices, or -1 for a chunk the gather reads straight from global memory.
 template <int M>
 __global__ void __launch_bounds__(512) chunk_local_kernel(const int32_t *__restrict__ simp, int64_t k,
@@ -445,7 +546,7 @@ __global__ void __launch_bounds__(512) chunk_local_kernel(const int32_t *__restr
             const int mid = (lo + hi) >> 1;
             if (keys[mid] < v) lo = mid + 1; else hi = mid;
         }
-        local[s0 * M + j] = (uint16_t)lo;
+        local[s0 * M + j] = (uint16_t)(lo * 64);          // byte offset of the vertex's window row
     }
 }
 
@@ -486,7 +587,6 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(
     int32_t *hist = reinterpret_cast<int32_t *>(smem);
     const size_t hbytes = ((size_t)NSPLIT * T * 128u + 15u) & ~(size_t)15u;
     const uint32_t histAddr = smem_addr(hist);
-    unsigned char *bufBase = smem + hbytes;
     const uint32_t bufAddr = histAddr + (uint32_t)hbytes;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const uint32_t histLane = histAddr + (uint32_t)lane * 4u;
@@ -546,17 +646,12 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(
         const int64_t s0 = c * C;
         const int ns = (int)(P.k - s0 < (int64_t)C ? P.k - s0 : (int64_t)C);
         if (u >= 0) {
-            const unsigned char *bb0 = bufBase + (size_t)buf * kStageBytes;
-            const uint16_t *wb = reinterpret_cast<const uint16_t *>(bb0) + lane;
-            const uint16_t *sid = reinterpret_cast<const uint16_t *>(bb0 + kWinBytes);
-            const int2 *swt = reinterpret_cast<const int2 *>(bb0 + kWinBytes + kIdBytes);
-            for (int bb = wid * GS; bb < ns; bb += nw * GS) {
-                const int n = min(GS, ns - bb);
-                if (n == GS)
-                    gather_group<NSPLIT, M, GS, true, true>(sid + bb * M, 0, swt + bb, n, wb, histLane, HOFF);
-                else
-                    gather_group<NSPLIT, M, GS, false, true>(sid + bb * M, 0, swt + bb, n, wb, histLane, HOFF);
-            }
+            const uint32_t b0 = bufAddr + (uint32_t)buf * kStageBytes;
+            const uint32_t winLane = b0 + 2u * (uint32_t)lane;
+            for (int bb = wid * GS; bb < ns; bb += nw * GS)
+                gather_group_staged<NSPLIT, M, GS>(b0 + kWinBytes + 2u * (uint32_t)(bb * M),
+                                                   b0 + kWinBytes + kIdBytes + 8u * (uint32_t)bb, min(GS, ns - bb),
+                                                   winLane, histLane, HOFF);
         } else {
             const uint16_t *gb = P.bins + lane;
             for (int bb = wid * GS; bb < ns; bb += nw * GS) {
