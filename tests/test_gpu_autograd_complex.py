@@ -117,3 +117,46 @@ def test_backward_f64_default_range_and_nonfinite_upstream(P, oracle):
     with pytest.raises(P.WectError):
         h.device_status()
     h.device_status()                  # cleared by the read
+
+
+def test_simplicial_gradient_matches_central_differences(P):
+    """Central differences (h = 2^-10 ~ 1e-3) of an MSE loss through ComplexWECTFunction on a
+    triangulated mesh, at vertices whose weight differs from every neighbour's by more than 2h
+    (away from ties the transform is linear in the weight, so the difference quotient is exact
+    up to float64 rounding): within 1e-6 relative of the autograd gradient."""
+    cx = S.jittered_grid_mesh(20, seed=38)
+    rng = np.random.default_rng(39)
+    # dyadic weights (multiples of 2^-10), so w +- h is exact in float32 and in 2^-24 fixed point
+    w = (np.floor(cx.weights.astype(np.float64) * 1024.0) / 1024.0).astype(np.float32)
+    t = (np.floor(rng.lognormal(0.0, 1.0, w.size) * 1024.0) / 1024.0).astype(np.float32)
+    dirs = S.circle_directions(16)
+    T, lo, hi = 64, -1.5, 1.5
+    sims = [cuda(s) for s in cx.simplices]
+    h = P.SimplicialComplex(cuda(cx.coords), sims, cuda(w), frac_bits=24)
+    ht = P.SimplicialComplex(cuda(cx.coords), sims, cuda(t), frac_bits=24)
+    B = ht.wect(cuda(dirs), T, lo, hi).to(torch.float64) * 2.0 ** -24
+
+    def loss_of(wv):
+        W = P.ComplexWECTFunction.apply(h, cuda(wv), cuda(dirs), T, lo, hi)
+        return float(((W - B) ** 2).mean())
+
+    g, _ = _mse_grad(P, h, w, B, dirs, T, lo, hi)
+    step = 2.0 ** -10
+    nbr = [set() for _ in range(w.size)]
+    for e in cx.simplices[0]:
+        nbr[int(e[0])].add(int(e[1]))
+        nbr[int(e[1])].add(int(e[0]))
+    free = [v for v in range(w.size) if nbr[v] and all(abs(float(w[v]) - float(w[u])) > 2 * step for u in nbr[v])]
+    assert len(free) >= 20
+    picked = [free[i] for i in rng.choice(len(free), 20, replace=False)]
+    checked = 0
+    for v in picked:
+        wp, wm = w.copy(), w.copy()
+        wp[v] += np.float32(step)
+        wm[v] -= np.float32(step)
+        fd = (loss_of(wp) - loss_of(wm)) / (2 * step)
+        if fd == 0.0 and g[v] == 0.0:
+            continue
+        assert abs(g[v] - fd) <= 1e-6 * max(abs(fd), abs(float(g[v]))), (v, g[v], fd)
+        checked += 1
+    assert checked >= 10
