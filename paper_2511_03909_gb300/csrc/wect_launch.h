@@ -143,16 +143,17 @@ cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, co
                                   int grid, cudaStream_t st);
 // Packed signed weights for the gather: v = sign * sw; nsplit 1: {v, 0}, 2: {v & 0xFFFF, v >> 16}.
 cudaError_t launch_pack_weights(const int64_t *sw, int64_t k, int sign, int nsplit, int2 *out, cudaStream_t st);
-// Stable sort of a list of k simplices (m vertices each, in place) by smallest vertex id; sw (may
-// be null) is permuted alike.  Creation time only: it allocates and synchronises the stream.
-// Morton code of every vertex (coordinates [nv][n], quantised on the box [-xm_a, xm_a]) and the
-// stable sort of a list by the smallest code among each simplex's vertices.
+// Morton code of every vertex (coordinates [nv][n], quantised on the box [-xm_a, xm_a]), and the
+// stable sort of a list of k simplices (m vertices each, in place) by the smallest code among each
+// simplex's vertices; sw (may be null) is permuted alike.  The sort is creation-time only: it
+// allocates and synchronises the stream.
 cudaError_t vertex_morton_keys(const double *coords, int64_t nv, int n, const double *xm, unsigned long long *vkey,
                                cudaStream_t st);
 cudaError_t sort_simplices_spatial(int32_t *simp, int64_t k, int m, int64_t *sw, const unsigned long long *vkey,
                                    cudaStream_t st);
 // Chunk-local ids of a list of k simplices with m vertices (m >= 2): per chunk its distinct vertices
-// (cverts, cnu) and the list rewritten in chunk-local 16-bit ids (local).
+// (cverts, cnu) and the list rewritten as the 16-bit byte offsets of their rows in the staged
+// window (local).
 cudaError_t launch_chunk_local(const int32_t *simp, int64_t k, int m, uint16_t *local, int32_t *cverts, int32_t *cnu,
                                cudaStream_t st);
 // The staged gather (two shared-memory windows of kWinRows vertex rows next to the histogram);
