@@ -102,27 +102,18 @@ __global__ void __launch_bounds__(256) vertex_bins_kernel(const double *__restri
 
 // ------------------------------------------------------------------ simplex scatter
 
-// Loads from global memory (read-only path) or, with SMEM, from shared memory.
-template <bool SMEM, typename T>
-__device__ __forceinline__ T ld_ro(const T *p)
-{
-    if (SMEM) return *p;
-    return __ldg(p);
-}
-
 // One warp's share of GS consecutive simplices (n valid; n == GS when FULL) in a 32-direction
-// tile.  All vertex ids, packed signed weights and vertex bins of the group are loaded before any
-// is reduced, so GS dependent load chains are in flight.  Vertex ids are global int32 ids, chunk-
-// local uint16 ids, or for M == 1 the simplex index itself (vbase + g).  With SMEM the ids, the
-// weights and the bins (a window of chunk vertices) are in shared memory.  bins and histLane
+// tile, read from global memory.  All vertex ids, packed signed weights and vertex bins of the
+// group are loaded before any is reduced, so GS dependent load chains are in flight.  Vertex ids
+// are global int32 ids, or for M == 1 the simplex index itself (vbase + g).  bins and histLane
 // already carry the lane's column; the max of the vertex bins (Eq. "msi") selects the histogram
-// row.
-// With GH the signed weight goes straight to the lane's int64 difference row orow in global memory
-// (null for a padding column) instead of the shared histogram.
-template <int NSPLIT, int M, int GS, bool FULL, bool SMEM, typename IdT, bool GH = false>
-__device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vbase, const int2 *__restrict__ wp, int n,
-                                             const uint16_t *__restrict__ bins, uint32_t histLane, uint32_t HOFF,
-                                             unsigned long long *orow = nullptr)
+// row.  With GH the signed weight goes straight to the lane's int64 difference row orow in global
+// memory (null for a padding column) instead of the shared histogram.  (Staged chunks take
+// gather_group_staged below.)
+template <int NSPLIT, int M, int GS, bool FULL, bool GH = false>
+__device__ __forceinline__ void gather_group(const int32_t *__restrict__ ids, int vbase, const int2 *__restrict__ wp,
+                                             int n, const uint16_t *__restrict__ bins, uint32_t histLane,
+                                             uint32_t HOFF, unsigned long long *orow = nullptr)
 {
     int vid[GS][M];
     int2 w[GS];
@@ -132,35 +123,18 @@ __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vb
         static_assert(GS == 8, "vector loads assume groups of 8");
 #pragma unroll
         for (int q = 0; q < GS / 2; ++q) {
-            const int4 x = ld_ro<SMEM>(reinterpret_cast<const int4 *>(wp) + q);
+            const int4 x = __ldg(reinterpret_cast<const int4 *>(wp) + q);
             w[2 * q] = make_int2(x.x, x.y);
             w[2 * q + 1] = make_int2(x.z, x.w);
         }
         if (M == 1) {
 #pragma unroll
             for (int g = 0; g < GS; ++g) vid[g][0] = vbase + g;
-        } else if (sizeof(IdT) == 2) {
-            uint32_t word[GS * M / 2];
-#pragma unroll
-            for (int q = 0; q < GS * M / 8; ++q) {
-                const uint4 x = ld_ro<SMEM>(reinterpret_cast<const uint4 *>(ids) + q);
-                word[4 * q] = x.x;
-                word[4 * q + 1] = x.y;
-                word[4 * q + 2] = x.z;
-                word[4 * q + 3] = x.w;
-            }
-#pragma unroll
-            for (int g = 0; g < GS; ++g)
-#pragma unroll
-                for (int j = 0; j < M; ++j) {
-                    const int e = g * M + j;
-                    vid[g][j] = (int)((word[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
-                }
         } else {
             int word[GS * M];
 #pragma unroll
             for (int q = 0; q < GS * M / 4; ++q) {
-                const int4 x = ld_ro<SMEM>(reinterpret_cast<const int4 *>(ids) + q);
+                const int4 x = __ldg(reinterpret_cast<const int4 *>(ids) + q);
                 word[4 * q] = x.x;
                 word[4 * q + 1] = x.y;
                 word[4 * q + 2] = x.z;
@@ -176,8 +150,8 @@ __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vb
         for (int g = 0; g < GS; ++g) {
             const int gi = min(g, n - 1);
 #pragma unroll
-            for (int j = 0; j < M; ++j) vid[g][j] = (M == 1) ? vbase + gi : (int)ld_ro<SMEM>(ids + gi * M + j);
-            w[g] = (g < n) ? ld_ro<SMEM>(wp + gi) : make_int2(0, 0);
+            for (int j = 0; j < M; ++j) vid[g][j] = (M == 1) ? vbase + gi : __ldg(ids + gi * M + j);
+            w[g] = (g < n) ? __ldg(wp + gi) : make_int2(0, 0);
         }
     }
     int bin[GS];
@@ -185,8 +159,7 @@ __device__ __forceinline__ void gather_group(const IdT *__restrict__ ids, int vb
     for (int g = 0; g < GS; ++g) {
         int bm = 0;
 #pragma unroll
-        for (int j = 0; j < M; ++j)
-            bm = max(bm, SMEM ? (int)bins[vid[g][j] * 32] : (int)__ldg(bins + (int64_t)vid[g][j] * 32));
+        for (int j = 0; j < M; ++j) bm = max(bm, (int)__ldg(bins + (int64_t)vid[g][j] * 32));
         bin[g] = bm;
     }
 #pragma unroll
@@ -328,10 +301,10 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const S
             const int n = (int)(b1 - bb < (int64_t)GS ? b1 - bb : (int64_t)GS);
             const int32_t *ids = (M == 1) ? nullptr : P.simp + bb * M;
             if (n == GS)
-                gather_group<NSPLIT, M, GS, true, false, int32_t, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
+                gather_group<NSPLIT, M, GS, true, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
                                                                       orow);
             else
-                gather_group<NSPLIT, M, GS, false, false, int32_t, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
+                gather_group<NSPLIT, M, GS, false, GH>(ids, (int)bb, P.swp + bb, n, bins, histLane, HOFF,
                                                                        orow);
         }
         if (!GH) simplex_flush<NSPLIT>(hist, T, P.dtile, P.d, P.out);
@@ -658,9 +631,9 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(
                 const int n = min(GS, ns - bb);
                 const int32_t *ids = P.simp + (s0 + bb) * M;
                 if (n == GS)
-                    gather_group<NSPLIT, M, GS, true, false>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
+                    gather_group<NSPLIT, M, GS, true>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
                 else
-                    gather_group<NSPLIT, M, GS, false, false>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
+                    gather_group<NSPLIT, M, GS, false>(ids, 0, P.swp + s0 + bb, n, gb, histLane, HOFF);
             }
         }
         __syncthreads();                        // buffer buf is free for chunk c + 2
