@@ -558,3 +558,55 @@ def test_brute_force_four_dimensional(oracle, dyadic):
         else:
             f = [height_reading(list(X[v]), list(dirs[p])) for v in range(nv)]
         assert got[p].tolist() == brute_wecf(nv, faces, weights, f, T, beta)
+
+
+# ----------------------------------------------------------------------- arbitrary filters (Algorithm 1, m filters)
+
+
+def test_wecf_simplicial_arbitrary_filters_brute_force(oracle):
+    """Algorithm 1 with m caller filters that are not heights (dyadic values, many of them
+    exactly on thresholds, repeated values, values outside the range): the oracle's WECF table
+    equals brute-force enumeration of every sublevel subcomplex with rational thresholds."""
+    for seed in range(4):
+        cx = S.random_simplicial(11, 2 + seed % 2, 16, 7, seed=300 + seed, coord_bits=3)
+        rng = np.random.default_rng(400 + seed)
+        m, T, lo, hi = 5, 17, -2.0, 2.0
+        f = rng.integers(-20, 21, size=(m, cx.nv)).astype(np.float64) / 8.0      # also beyond [lo, hi]
+        vw = cx.weights.astype(np.int64)
+        got = oracle.wecf_simplicial(f, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), T, lo, hi)
+        faces, weights = simplicial_faces(cx, vw)
+        beta = [Fraction(lo) + q * (Fraction(hi) - Fraction(lo)) / (T - 1) for q in range(T)]
+        for p in range(m):
+            fr = [Fraction(x) for x in f[p]]
+            assert got[p].tolist() == brute_wecf(cx.nv, faces, weights, fr, T, beta)
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_wecf_cubical_arbitrary_filters_brute_force(oracle, weighted):
+    """The grid WECF (and unweighted ECF) of caller filters against brute force over every box
+    of the grid; the cell weight is the max of its vertex weights, or 1 unweighted."""
+    for dims in ([5, 4], [3, 3, 2]):
+        rng = np.random.default_rng(500 + len(dims))
+        nv = int(np.prod(dims))
+        vw = rng.integers(-3, 12, nv).astype(np.int64)
+        m, T, lo, hi = 4, 9, -1.0, 1.0
+        f = rng.integers(-10, 11, size=(m, nv)).astype(np.float64) / 8.0
+        got = oracle.wecf_cubical(dims, vw, f, T, lo, hi, weighted=weighted)
+        cells = cubical_cells(dims)
+        weights = [max(int(vw[v]) for v in c) if weighted else 1 for c in cells]
+        beta = [Fraction(lo) + q * (Fraction(hi) - Fraction(lo)) / (T - 1) for q in range(T)]
+        for p in range(m):
+            fr = [Fraction(x) for x in f[p]]
+            assert got[p].tolist() == brute_wecf(nv, cells, weights, fr, T, beta, cubical=True)
+
+
+def test_wecf_of_height_filters_is_the_wect(oracle):
+    """Algorithm 1 fed the oracle's own float64 heights as filters gives the WECT table."""
+    cx = S.random_simplicial(40, 3, 90, 60, seed=601)
+    dirs = S.random_directions(6, 3, seed=602)
+    vw = cx.weights.astype(np.int64)
+    sw = oracle.simplicial_weights(cx.simplices, vw)
+    T, lo, hi = 23, -1.7, 1.9
+    f = np.array([[oracle.height(cx.coords[v], dirs[p]) for v in range(cx.nv)] for p in range(len(dirs))])
+    assert np.array_equal(oracle.wecf_simplicial(f, cx.simplices, sw, T, lo, hi),
+                          oracle.wect_simplicial(cx.coords, cx.simplices, sw, dirs, T, lo, hi))
