@@ -162,10 +162,10 @@ WECT_API void wect_complex_destroy(wect_complex cx);
  *               device); otherwise lo <= hi, finite.
  *   out (dev)   [d][T] int64, row p = WECF of direction p at thresholds beta[0..T-1]
  * Errors: INVALID_ARG for NULL pointers, d < 1, T < 2 or a bad range; UNSUPPORTED for
- * T > 65535, or on a cubical grid whose axis-0 rows are longer than the stencil kernel's shared
- * row buffers hold (about 800 vertices for n = 3, 1,600 for n = 2, 3,200 for n = 1).  Every
- * T up to 65535 is supported: when the int32 histograms of a direction tile do not fit shared
- * memory, the kernels add each update to the int64 table in global memory instead.
+ * T > 65535.  Every T up to 65535 is supported: when the int32 histograms of a direction tile do
+ * not fit shared memory, the kernels add each update to the int64 table in global memory
+ * instead.  Any axis-0 row length is supported: on a cubical grid, rows longer than 512
+ * vertices are walked in segments of 512.
  */
 WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
                          int64_t *out, wect_stream stream);

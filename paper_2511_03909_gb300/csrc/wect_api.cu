@@ -286,8 +286,9 @@ struct wect_batch_s {
     int64_t climit = 0;
     int kflush = 1 << 16;
     int64_t total_nv = 0;
-    int maxL0 = 1;
-    double meanL0 = 1.0;           // mean row length over all rows of the batch
+    int maxL0 = 1;                 // longest unit of the forward stencil kernel (a row or a segment)
+    double meanL0 = 1.0;           // mean unit length over all units of the batch
+    bool segmented = false;        // some grid's rows are walked in segments
     std::vector<GridDesc> h_grids;
     std::vector<int64_t> v_off;
     GridDesc *d_grids = nullptr;
@@ -412,7 +413,8 @@ static bool run_shape(int n, int d, int T, int maxL0, CubShape &out, int Dt_req 
 // With run_ok (one histogram plane) the run-based kernel is taken when it is estimated cheaper
 // (meanL0 rows, a threshold range of width span), or always under the test hook.
 static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out, int dpl_req = 0, int Dt_req = 0,
-                      double meanL0 = 0.0, double span = 0.0, int threads_req = 0, bool tma_ok = false)
+                      double meanL0 = 0.0, double span = 0.0, int threads_req = 0, bool tma_ok = false,
+                      bool segmented = false)
 {
     const int threads = threads_req > 0 ? threads_req : cubical_fwd_threads();
     const int warps = threads / 32;
@@ -423,7 +425,9 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     const int L0s = (tma_ok && g_stencil_variant.load() != 3) ? cubical_fwd_stage_len(n, maxL0) : 0;
     const size_t limit = smem_optin() - 1024;
     out.run = false;
-    if (nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1 && g_stencil_variant.load() != 3) {
+    // (the run-based kernel walks whole rows: not for grids walked in segments)
+    if (!segmented && nsplit == 1 && dpl_req == 0 && Dt_req == 0 && g_stencil_variant.load() != 1 &&
+        g_stencil_variant.load() != 3) {
         const bool want = g_stencil_variant.load() == 2 ||
                           run_profitable(n, meanL0 > 0.0 ? meanL0 : (double)maxL0, T, span);
         if (want && run_shape(n, d, T, maxL0, out)) return true;
@@ -482,31 +486,55 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
 // Items for a set of grids: per complex, direction tiles x row chunks, largest first.  An item
 // never holds more than kflush vertices (the int32 histogram bound); whole=true keeps one chunk
 // per complex (the caller has checked that every complex fits).
+// Axis-0 rows longer than seg_len(n, nsplit) vertices are walked by the forward stencil kernel in
+// segments of that length (each a unit of work with its own shared row of octant contributions);
+// shorter rows are whole units.  The length keeps the row buffers of the worst-case shape (16 row
+// groups of one warp, NSPLIT planes of 2^n octant rows) within 128 KB, so every grid has a shape
+// (with the global histogram when the shared one no longer fits beside them).
+static int seg_len(int n, int nsplit)
+{
+    const int base = (n >= 3) ? 256 : (n == 2 ? 512 : 1024);
+    return nsplit >= 2 ? base / 2 : base;
+}
+
+static void set_segments(GridDesc &g, int n, int nsplit)
+{
+    const int S = seg_len(n, nsplit);
+    g.seg = (g.L[0] > S) ? S : 0;
+    g.nseg = (g.L[0] > S) ? (g.L[0] + S - 1) / S : 1;
+}
+
+// Vertices of one unit (a row, or a segment of one) of the forward stencil kernel.
+static int unit_len(const GridDesc &g) { return g.seg > 0 ? g.seg : g.L[0]; }
+
 static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int T, int kflush,
                                         int target_items, bool whole)
 {
     const int ntiles = (d + Dt - 1) / Dt;
     std::vector<std::pair<int64_t, WorkItem>> v;
-    int64_t total_rows = 0;
-    for (auto &g : grids) total_rows += g.rows;
+    // items are ranges of units: rows, or row segments of long rows (unit u = row u / nseg,
+    // segment u % nseg)
+    int64_t total_units = 0;
+    for (auto &g : grids) total_units += (int64_t)g.rows * g.nseg;
     for (int c = 0; c < (int)grids.size(); ++c) {
         const GridDesc &g = grids[c];
-        const int max_rows = std::max(1, kflush / std::max(1, g.L[0]));
+        const int units = g.rows * g.nseg, ul = unit_len(g);
+        const int max_units = std::max(1, kflush / std::max(1, ul));
         int chunks = 1;
         if (!whole) {
-            const double share = (double)g.rows / (double)std::max<int64_t>(total_rows, 1);
+            const double share = (double)units / (double)std::max<int64_t>(total_units, 1);
             chunks = (int)std::ceil(share * target_items / ntiles);
-            // no item smaller than 8x its histogram flush (T x Dt entries): rows * L0 >= 8 T
-            const int min_rows = (int)std::min<int64_t>(g.rows, (8ll * T + g.L[0] - 1) / std::max(1, g.L[0]));
-            chunks = std::min(chunks, std::max(1, g.rows / std::max(1, min_rows)));
-            chunks = std::max(chunks, (g.rows + max_rows - 1) / max_rows);
-            chunks = std::max(1, std::min(chunks, g.rows));
+            // no item smaller than 8x its histogram flush (T x Dt entries): units * length >= 8 T
+            const int min_units = (int)std::min<int64_t>(units, (8ll * T + ul - 1) / std::max(1, ul));
+            chunks = std::min(chunks, std::max(1, units / std::max(1, min_units)));
+            chunks = std::max(chunks, (units + max_units - 1) / max_units);
+            chunks = std::max(1, std::min(chunks, units));
         }
-        const int per = (g.rows + chunks - 1) / chunks;
+        const int per = (units + chunks - 1) / chunks;
         for (int t = 0; t < ntiles; ++t)
-            for (int r0 = 0; r0 < g.rows; r0 += per) {
-                WorkItem w{c, t, r0, std::min(g.rows, r0 + per)};
-                v.push_back({(int64_t)(w.r1 - w.r0) * g.L[0], w});
+            for (int r0 = 0; r0 < units; r0 += per) {
+                WorkItem w{c, t, r0, std::min(units, r0 + per)};
+                v.push_back({(int64_t)(w.r1 - w.r0) * ul, w});
             }
     }
     std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
@@ -519,11 +547,12 @@ static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int 
 // ------------------------------------------------------------------ cubical launch sequence
 
 struct CubLaunch {
-    int n, nsplit, wt, frac_bits, kflush, maxL0;
+    int n, nsplit, wt, frac_bits, kflush, maxL0;   // maxL0: longest unit (row or row segment)
     int64_t climit;
     const GridDesc *d_grids;
     Workspace *ws;
     int *status;                  // device status word (non-finite directions are flagged here)
+    bool segmented = false;       // some grid walks its rows in segments
 };
 
 // Enqueue the forward transform of a set of grids: [range], beta, work queue, stencil kernel,
@@ -560,6 +589,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.out = reinterpret_cast<unsigned long long *>(out);
     a.threads = sh.threads;
     a.L0s = sh.L0s;
+    a.segmented = L.segmented ? 1 : 0;
     const int grid = std::max(1, std::min(sh.grid, n_items));
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -713,6 +743,7 @@ extern "C" wect_status wect_complex_create_cubical(int n, const int64_t *dims, c
     g.w = c->d_w32;
     for (int a = 0; a < 3; ++a) g.L[a] = c->L[a];
     g.rows = c->L[1] * c->L[2];
+    set_segments(g, n, c->nsplit);
     g.nv = nv;
     g.v_off = 0;
     g.status = c->d_status;
@@ -987,24 +1018,28 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
                                    cudaStream_t st)
 {
     CubShape sh;
-    if (!cub_shape(c->n, c->nsplit, d, T, c->L[0], sh, 0, 0, (double)c->L[0], hi - lo, 0, c->d_tmap != nullptr))
-        return fail(WECT_ERR_UNSUPPORTED, "grid rows of %d vertices do not fit the kernel's shared row buffers", c->L[0]);
-    if (c->L[0] > c->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
+    GridDesc gd{};
+    gd.L[0] = c->L[0]; gd.L[1] = c->L[1]; gd.L[2] = c->L[2];
+    gd.rows = c->L[1] * c->L[2];
+    gd.nv = c->nv;
+    set_segments(gd, c->n, c->nsplit);
+    const int ul = unit_len(gd);
+    if (!cub_shape(c->n, c->nsplit, d, T, ul, sh, 0, 0, (double)ul, hi - lo, 0, c->d_tmap != nullptr && gd.nseg == 1,
+                   gd.nseg > 1))
+        return fail(WECT_ERR_UNSUPPORTED, "grid rows of %d vertices do not fit the kernel's shared row buffers", ul);
+    if (ul > c->kflush && !sh.gh) return fail(WECT_ERR_UNSUPPORTED, "grid rows longer than %d vertices", c->kflush);
     wect_status s = ensure_common_ws(c->ws, T, d);
     if (s) return s;
-    const int rows = c->L[1] * c->L[2];
     const bool direct = false;
     auto key = std::make_tuple(d, T, sh.Dt, sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1), sh.grid);
     if (c->ws.items_key != key) {   // (items do not depend on the TMA staging)
-        std::vector<GridDesc> gv(1);
-        gv[0].L[0] = c->L[0]; gv[0].L[1] = c->L[1]; gv[0].L[2] = c->L[2];
-        gv[0].rows = rows;
-        gv[0].nv = c->nv;
+        std::vector<GridDesc> gv(1, gd);
         std::vector<WorkItem> items = make_items(gv, d, sh.Dt, T, c->kflush, sh.grid, false);
         if ((s = upload_items(c->ws, items, st))) return s;
         c->ws.items_key = key;
     }
-    CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, c->L[0], c->climit, c->d_grid, &c->ws, c->d_status};
+    CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, ul, c->climit, c->d_grid, &c->ws, c->d_status,
+                gd.nseg > 1};
     return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st);
 }
 
@@ -1365,15 +1400,17 @@ static wect_status batch_finish(wect_batch b, cudaStream_t st)
     int64_t off = 0;
     b->maxL0 = 1;
     for (int i = 0; i < b->count; ++i) {
+        set_segments(b->h_grids[i], b->n, b->nsplit);       // with the batch's accumulator mode
         b->h_grids[i].v_off = off;
         b->v_off[i] = off;
         off += b->h_grids[i].nv;
-        b->maxL0 = std::max(b->maxL0, b->h_grids[i].L[0]);
+        b->maxL0 = std::max(b->maxL0, unit_len(b->h_grids[i]));
+        b->segmented = b->segmented || b->h_grids[i].nseg > 1;
     }
     b->total_nv = off;
-    int64_t rows = 0;
-    for (auto &g : b->h_grids) rows += g.rows;
-    b->meanL0 = (double)off / (double)std::max<int64_t>(rows, 1);
+    int64_t units = 0;
+    for (auto &g : b->h_grids) units += (int64_t)g.rows * g.nseg;
+    b->meanL0 = (double)off / (double)std::max<int64_t>(units, 1);
     CK(dev_malloc((void **)&b->d_grids, b->h_grids.size() * sizeof(GridDesc)), "alloc grids");
     CK(cudaMemcpy(b->d_grids, b->h_grids.data(), b->h_grids.size() * sizeof(GridDesc), cudaMemcpyHostToDevice), "upload grids");
     CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
@@ -1556,11 +1593,11 @@ static bool batch_shape(wect_batch b, int d, int T, double span, CubShape &sh)
 {
     auto it = b->tuned.find({d, T});
     if (it != b->tuned.end()) {
-        if (it->second.run) return b->nsplit == 1 && run_shape(b->n, d, T, b->maxL0, sh, it->second.Dt);
+        if (it->second.run) return !b->segmented && b->nsplit == 1 && run_shape(b->n, d, T, b->maxL0, sh, it->second.Dt);
         return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, it->second.dpl, it->second.Dt, 0.0, 0.0,
-                         it->second.threads, b->has_tmap);
+                         it->second.threads, b->has_tmap, b->segmented);
     }
-    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span, 0, b->has_tmap);
+    return cub_shape(b->n, b->nsplit, d, T, b->maxL0, sh, 0, 0, b->meanL0, span, 0, b->has_tmap, b->segmented);
 }
 
 // Tile-shape code for cache keys: dpl, negative for the global-histogram variant, 100 for runs.
@@ -1589,7 +1626,8 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
 static wect_status batch_enqueue(wect_batch b, const CubShape &sh, bool direct, const double *dirs, int d, int T,
                                  double lo, double hi, int64_t *out, cudaStream_t st)
 {
-    CubLaunch L{b->n, b->nsplit, b->wtype, b->frac_bits, b->kflush, b->maxL0, b->climit, b->d_grids, &b->ws, b->d_status};
+    CubLaunch L{b->n, b->nsplit, b->wtype, b->frac_bits, b->kflush, b->maxL0, b->climit, b->d_grids, &b->ws, b->d_status,
+                b->segmented};
     return enqueue_cubical_fwd(L, sh, b->ws.n_items, direct, dirs, d, T, lo, hi, false, (int64_t)b->count * d, out, st);
 }
 
@@ -1707,6 +1745,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.out = reinterpret_cast<unsigned long long *>(out);
         a.threads = sh.threads;
         a.L0s = sh.L0s;
+        a.segmented = b->h_grids[i].nseg > 1 ? 1 : 0;
         const int grid = std::max(1, std::min(sh.grid, a.n_items));
         KL(sh.run ? launch_cubical_run(b->n, a, grid, sh.smem, st)
                   : launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st),
@@ -1772,7 +1811,7 @@ extern "C" wect_status wect_batch_autotune(wect_batch b, const double *dirs, int
     for (int threads : {512, 256})
         for (int dpl : {1, 2, 4})
             for (int Dt = 32 * dpl; Dt <= 32 * dpl * (threads / 32); Dt *= 2) cands.push_back({dpl, Dt, false, threads});
-    if (b->nsplit == 1)
+    if (b->nsplit == 1 && !b->segmented)
         for (int Dt = 32; Dt <= 256; Dt *= 2) cands.push_back({1, Dt, true, cubical_run_threads()});
     (void)warps;
     cudaEvent_t e0, e1;

@@ -73,7 +73,7 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
 // (regular grids seen along axis or diagonal directions) no longer serialise the warp.
 template <int N, int NSPLIT, int DPL, bool GH>
 __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow,
-                                                 int CP, int i0, int i1, int i2, uint32_t pend, float k0,
+                                                 int CP, int i0, int x0, int i1, int i2, uint32_t pend, float k0,
                                                  const DirFilter *dirf, int colbase, int pbase, uint32_t histAddr,
                                                  int Dt, uint32_t HOFF, uint32_t *wq, unsigned long long *oc)
 {
@@ -107,18 +107,19 @@ __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const 
             const int cv = crow[f.oct * CP + i0 + u];
             const int hv = (NSPLIT == 2) ? crow[NOCT * CP + f.oct * CP + i0 + u] : 0;
             const int p = (pbase + col < P.d) ? P.perm[pbase + col] : P.d;
-            cubical_fixup<N, NSPLIT, GH>(P, g, p, i0 + u, i1, i2, thi, rf.nr, col, histAddr, Dt, HOFF, cv, hv, oc);
+            cubical_fixup<N, NSPLIT, GH>(P, g, p, x0 + i0 + u, i1, i2, thi, rf.nr, col, histAddr, Dt, HOFF, cv, hv, oc);
         }
         __syncwarp();
     }
 }
 
-// One grid row for the DPL directions of each lane.  CLAMP selects the variant whose bins may
-// leave [0, T-1] (heights outside the threshold range); the other variant has been proven
-// in range for the whole row and skips the clamp.
+// One unit of a grid row (the whole row, or L0 vertices of it from x0 on when long rows are walked
+// in segments; Lfull is the row's length) for the DPL directions of each lane.  CLAMP selects the
+// variant whose bins may leave [0, T-1] (heights outside the threshold range); the other variant
+// has been proven in range for the whole row and skips the clamp.
 template <int N, int NSPLIT, int DPL, bool CLAMP, bool GH>
 __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow, int CP, int L0,
-                                        int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
+                                        int x0, int Lfull, int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
                                         const int (&oct)[DPL], const int (&col)[DPL], int pbase, uint32_t histAddr,
                                         int Dt, uint32_t HOFF, const DirFilter *dirf, int colbase, uint32_t *wq,
                                         unsigned long long *const (&orow)[DPL], unsigned long long *oc)
@@ -135,7 +136,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
         hb[j] = histAddr + (uint32_t)col[j] * 4u + (CLAMP ? 0u : (uint32_t)(rf[j].nr - kMagicBits) * D4);
     }
     const int LU = L0 - L0 % U;
-    float k0 = (float)(1 - L0);
+    float k0 = (float)(2 * x0 + 1 - Lfull);            // k = 2 x - (Lfull - 1) of the unit's first vertex
     // packed copies of the per-row constants for the f32x2 path
     constexpr int NP = (DPL % 2 == 0) ? DPL / 2 : 1;
     F2 S0p[NP], Glop[NP], Ghip[NP];
@@ -217,8 +218,8 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                     filter_ceil(k0 + 2.0f * (float)u, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
                     if (tlo != thi) pend |= 1u << (u * DPL + j);
                 }
-            cubical_fixup_block<N, NSPLIT, DPL, GH>(P, g, crow, CP, i0, i1, i2, pend, k0, dirf, colbase, pbase, histAddr,
-                                                    Dt, HOFF, wq, oc);
+            cubical_fixup_block<N, NSPLIT, DPL, GH>(P, g, crow, CP, i0, x0, i1, i2, pend, k0, dirf, colbase, pbase,
+                                                    histAddr, Dt, HOFF, wq, oc);
         }
         k0 += 2.0f * (float)U;
         k02 = kk2;
@@ -245,7 +246,8 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             }
             if (tlo != thi) {
                 const int p = (pbase + col[j] < P.d) ? P.perm[pbase + col[j]] : P.d;
-                cubical_fixup<N, NSPLIT, GH>(P, g, p, i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF, cvs, hvs, oc);
+                cubical_fixup<N, NSPLIT, GH>(P, g, p, x0 + i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF, cvs, hvs,
+                                             oc);
             }
         }
         k0 += 2.0f;
@@ -254,7 +256,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
 
 // ------------------------------------------------------------------ forward
 
-template <int N, int NSPLIT, int DPL, bool GH>
+template <int N, int NSPLIT, int DPL, bool GH, bool SEG>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
 {
     constexpr int NOCT = 1 << N;
@@ -341,7 +343,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 
         // ---- each row group walks rows r0 + rgroup, r0 + rgroup + RG, ... with a double-buffered
         // row of octant contributions (one group barrier per row, no block-wide barrier)
-        const bool tma = (N >= 2) && P.L0s > 0 && g.tmap != nullptr;
+        // (a grid walked in segments is never staged: its box would not fit the stage)
+        const bool tma = (N >= 2) && P.L0s > 0 && g.tmap != nullptr && (!SEG || g.nseg == 1);
         const uint32_t boxBytes = (uint32_t)(NROWS * L0) * 4u;
         // box of the rows around row r' (rows outside the grid come back as zeros)
         auto stage_row = [&](int rr, unsigned kb) {
@@ -355,7 +358,13 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         for (int r = W.r0 + rgroup; r < W.r1; r += RG, parity ^= 1) {
             int32_t *crow = cgrp + (nbuf == 2 ? parity : 0) * rowbuf;
             if (nbuf == 1) __syncwarp();        // the previous row's reads are done before the rewrite
-            const int i1 = r % L1, i2 = r / L1;
+            // unit r: grid row rr, or (SEG instances only) its segment of Lu vertices from x0 when
+            // the grid's rows are walked in segments (such grids are not TMA-staged)
+            const bool segd = SEG && g.nseg > 1;
+            const int rr = segd ? r / g.nseg : r;
+            const int x0 = segd ? (r - rr * g.nseg) * g.seg : 0;
+            const int Lu = segd ? min(g.seg, L0 - x0) : L0;
+            const int i1 = rr % L1, i2 = rr / L1;
             const unsigned k = krow;
             const int32_t *box = stage + (size_t)(k & 1u) * NROWS * P.L0s;
             if (tma) {
@@ -365,12 +374,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
                 if (gtid == 0 && r + RG < W.r1) stage_row(r + RG, k + 1);
                 if (!mbar_wait_bounded((k & 1u) ? mbar1 : mbar0, (k >> 1) & 1u)) atomicOr(g.status, kStatusTimeout);
             }
-            for (int i0 = gtid; i0 < L0; i0 += gthreads) {
+            for (int i0 = gtid; i0 < Lu; i0 += gthreads) {
                 int32_t c[NOCT];
                 if (tma)
                     octant_contribs_box<N>(box, g, i0, i1, i2, c);
                 else
-                    octant_contribs<N>(g, i0, i1, i2, c);
+                    octant_contribs<N>(g, x0 + i0, i1, i2, c);
 #pragma unroll
                 for (int o = 0; o < NOCT; ++o) {
                     const int32_t v = c[o];
@@ -402,14 +411,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
                 clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
             }
             if constexpr (GH) {
-                fwd_row<N, NSPLIT, DPL, true, true>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                fwd_row<N, NSPLIT, DPL, true, true>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
                                                     HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
             } else {
                 if (__any_sync(0xffffffffu, clampRow))
-                    fwd_row<N, NSPLIT, DPL, true, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                    fwd_row<N, NSPLIT, DPL, true, false>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
                                                          HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
                 else
-                    fwd_row<N, NSPLIT, DPL, false, false>(P, g, crow, CP, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
+                    fwd_row<N, NSPLIT, DPL, false, false>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
                                                           Dt, HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
             }
         }
@@ -445,20 +454,33 @@ __global__ void grid_max_abs_kernel(const GridDesc *grids, const double *dirs, i
 
 // The dynamic shared-memory opt-in is set once per kernel instance and size (never inside a
 // stream capture once a size has been seen).
-template <int N, int NSPLIT, int DPL, bool GH>
-static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
+template <int N, int NSPLIT, int DPL, bool GH, bool SEG>
+static cudaError_t launch_fwd_s(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL, GH>,
+        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL, GH, SEG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         done = smem;
     }
     if (!launch) return cudaSuccess;
     const int threads = (a.threads > 0 && a.threads <= kFwdThreads) ? a.threads : kFwdThreads;
-    cubical_fwd_kernel<N, NSPLIT, DPL, GH><<<grid, threads, smem, st>>>(a);
+    cubical_fwd_kernel<N, NSPLIT, DPL, GH, SEG><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// The instance that walks segments of long rows only when some grid of the launch needs it (the
+// other keeps the row loop free of the unit decoding); preparing sets up both.
+template <int N, int NSPLIT, int DPL, bool GH>
+static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
+{
+    if (!launch) {
+        cudaError_t e = launch_fwd_s<N, NSPLIT, DPL, GH, false>(a, grid, smem, st, false);
+        return e != cudaSuccess ? e : launch_fwd_s<N, NSPLIT, DPL, GH, true>(a, grid, smem, st, false);
+    }
+    return a.segmented ? launch_fwd_s<N, NSPLIT, DPL, GH, true>(a, grid, smem, st, true)
+                       : launch_fwd_s<N, NSPLIT, DPL, GH, false>(a, grid, smem, st, true);
 }
 
 template <int N, int NSPLIT>

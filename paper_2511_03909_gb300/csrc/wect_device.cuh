@@ -43,6 +43,10 @@ struct GridDesc {
     int *status;         // device status word of the complex
     const double *xg;    // grid coordinates [L0 + L1 + L2] (axis 0, then 1, then 2), or null
     const void *tmap;    // TMA tensor map of w as a 3-D [L2][L1][L0] int32 tensor, or null
+    // the forward stencil kernel walks axis-0 rows in segments of seg vertices (nseg per row)
+    // when the rows are longer than its shared row buffers; seg = 0: whole rows
+    int seg = 0;
+    int nseg = 1;
 };
 
 // A unit of work of the cubical kernels: one complex, one direction tile, a row range.

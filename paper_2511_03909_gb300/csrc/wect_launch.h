@@ -27,6 +27,7 @@ struct CubicalFwdArgs {
     int threads;                  // CTA size of the per-vertex stencil kernel (256 or 512; 0 = 512)
     int L0s;                      // > 0: rows are staged by TMA from grids with a tensor map, into
                                   // per-row-group buffers of 2 x 3^(n-1) rows of L0s int32
+    int segmented;                // some grid walks its rows in segments (GridDesc::seg, nseg)
 };
 
 struct CubicalBwdArgs {
