@@ -20,7 +20,8 @@
 // histograms are flushed into the int64 output with global atomics (exact, order-free).  When
 // T x Dt int32 entries no longer fit shared memory (large T), the GH variant scatters every
 // update straight into the int64 difference table in global memory instead (same bins, same
-// integer sums; slower, but any T).
+// integer sums; slower, but any T).  Rows longer than the shared row buffers are walked in
+// segments (GridDesc::seg), each segment a unit of work with its own row of contributions.
 #include <cuda.h>
 
 #include <mutex>
