@@ -489,11 +489,12 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
 // Axis-0 rows longer than seg_len(n, nsplit) vertices are walked by the forward stencil kernel in
 // segments of that length (each a unit of work with its own shared row of octant contributions);
 // shorter rows are whole units.  The length keeps the row buffers of the worst-case shape (16 row
-// groups of one warp, NSPLIT planes of 2^n octant rows) within 128 KB, so every grid has a shape
-// (with the global histogram when the shared one no longer fits beside them).
+// groups of one warp, NSPLIT planes of 2^n octant rows) within 128 KB for n = 3 and 64 KB for
+// n = 1, 2, so every grid has a shape, and a one-warp direction tile keeps its shared histogram
+// up to T ~ 1000 beside them (beyond, the global histogram).
 static int seg_len(int n, int nsplit)
 {
-    const int base = (n >= 3) ? 256 : (n == 2 ? 512 : 1024);
+    const int base = (n >= 2) ? 256 : 512;
     return nsplit >= 2 ? base / 2 : base;
 }
 
