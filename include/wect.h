@@ -162,10 +162,12 @@ WECT_API void wect_complex_destroy(wect_complex cx);
  *               device); otherwise lo <= hi, finite.
  *   out (dev)   [d][T] int64, row p = WECF of direction p at thresholds beta[0..T-1]
  * Errors: INVALID_ARG for NULL pointers, d < 1, T < 2 or a bad range; UNSUPPORTED for
- * T > 65535.  Every T up to 65535 is supported: when the int32 histograms of a direction tile do
- * not fit shared memory, the kernels add each update to the int64 table in global memory
- * instead.  Any axis-0 row length is supported: on a cubical grid, rows longer than 512
- * vertices are walked in segments of 512.
+ * T > 65535.  Every T up to 65535 is supported.  On a cubical grid, when the int32 histogram of
+ * all T thresholds of a direction tile does not fit shared memory, the stencil kernel makes one
+ * pass per threshold tile (a band of bins with a discard row on each side); a simplicial
+ * complex's gather adds each update to the int64 table in global memory instead.  Any axis-0
+ * row length is supported: on a cubical grid, rows longer than 256 vertices (512 for n = 1,
+ * half that for two-plane weights) are walked in segments.
  */
 WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, int T, double lo, double hi,
                          int64_t *out, wect_stream stream);
@@ -292,8 +294,8 @@ WECT_API wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, i
  * Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest:
  * for the per-vertex stencil kernel every tile width Dt (32 .. 32 x directions per lane x warps),
  * 1, 2 or 4 directions per lane, and CTAs of 512 or 256 threads; for the run-based kernel (one
- * histogram plane) Dt = 32 .. 256.  When no shared-histogram shape fits T, the global-histogram
- * shape stays.  wect_batch_tuned_shape reports the choice.
+ * histogram plane) Dt = 32 .. 256.  When no shape holds all T thresholds in shared memory, the
+ * threshold-tiled default shape stays.  wect_batch_tuned_shape reports the choice.
  */
 WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                 int64_t *scratch_out, wect_stream stream);

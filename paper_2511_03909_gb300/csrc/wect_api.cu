@@ -360,6 +360,7 @@ struct CubShape {
     bool run = false;             // run-based kernel (walks bin boundaries along the rows)
     int threads = 512;            // CTA size
     int L0s = 0;                  // > 0: TMA staging of the neighbouring rows (per-vertex kernel)
+    int Tt = 0;                   // > 0: threshold tiles of Tt bins, one pass over the grid each
 };
 
 
@@ -420,6 +421,7 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     const int warps = threads / 32;
     out.threads = threads;
     out.L0s = 0;
+    out.Tt = 0;
     // TMA staging of the neighbouring rows when some grid has a tensor map and it fits next to
     // the histogram (else plain loads)
     const int L0s = (tma_ok && g_stencil_variant.load() != 3) ? cubical_fwd_stage_len(n, maxL0) : 0;
@@ -463,7 +465,54 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
         if (Dt_req > 0) break;
     }
     if (dpl_req > 0 || Dt_req > 0) return false;
-    // no shared histogram fits: scatter into the global int64 difference table instead
+    // no shared histogram of all T rows fits: threshold tiles of Tt bins (plus a discard row on
+    // each side), one pass over the grid per (direction tile, threshold tile).  A pass costs a
+    // per-vertex part (octant contributions, row set-up) and a per-update part; measured on the
+    // 128^3 volume (T = 128, 512, 1024 at tile widths 256, 64, 32) they weigh about 45 : 1 per
+    // direction, so the cost is passes x (45 + Dt).  The cheapest shape wins (ties: the first,
+    // widest), and it beats the global histogram.
+    {
+        int64_t bestCost = INT64_MAX;
+        CubShape best;
+        for (int Dt = Dmax; Dt >= 32; Dt /= 2)
+            for (int dpl : {2, 4, 1}) {
+                if (Dt % (32 * dpl)) continue;
+                const int WC = Dt / (32 * dpl);
+                if (WC > warps || warps % WC) continue;
+                if (dpl > 1 && Dt / dpl < 32) continue;
+                const size_t fixed = cubical_fwd_smem(n, nsplit, dpl, 0, Dt, maxL0, false, threads);
+                if (fixed >= limit) continue;
+                int Tt = (int)((limit - fixed) / ((size_t)nsplit * Dt * 4u)) - 2;
+                if (Tt < 16) continue;
+                Tt = std::min(Tt, T);
+                const int64_t cost = (int64_t)((d + Dt - 1) / Dt) * ((T + Tt - 1) / Tt) * (45 + Dt);
+                if (cost >= bestCost) continue;
+                bestCost = cost;
+                best = CubShape{};
+                best.threads = threads;
+                best.dpl = dpl;
+                best.Dt = Dt;
+                best.Tt = Tt;
+                best.smem = cubical_fwd_smem(n, nsplit, dpl, Tt + 2, Dt, maxL0, false, threads);
+                if (L0s > 0) {
+                    const size_t smt = cubical_fwd_smem(n, nsplit, dpl, Tt + 2, Dt, maxL0, false, threads, L0s);
+                    if (smt <= limit) {
+                        best.smem = smt;
+                        best.L0s = L0s;
+                    }
+                }
+            }
+        if (bestCost < INT64_MAX) {
+            out = best;
+            const int k = ctas_per_sm_for(out.smem, threads);
+            out.ctas_per_sm = k;
+            out.grid = sm_count() * k;
+            out.gh = false;
+            out.run = false;
+            return true;
+        }
+    }
+    // not even threshold tiles fit: scatter into the global int64 difference table instead
     const int Dt = std::min(Dmax, 256);
     out.dpl = Dt >= 64 ? 2 : 1;
     out.Dt = Dt;
@@ -509,9 +558,12 @@ static void set_segments(GridDesc &g, int n, int nsplit)
 static int unit_len(const GridDesc &g) { return g.seg > 0 ? g.seg : g.L[0]; }
 
 static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int d, int Dt, int T, int kflush,
-                                        int target_items, bool whole)
+                                        int target_items, bool whole, int Tt = 0)
 {
-    const int ntiles = (d + Dt - 1) / Dt;
+    // direction tiles x threshold tiles (Tt > 0: each item covers Tt bins of one tile)
+    const int nttiles = (Tt > 0) ? (T + Tt - 1) / Tt : 1;
+    const int ntiles = (d + Dt - 1) / Dt * nttiles;
+    const int HR = (Tt > 0) ? std::min(T, Tt + 2) : T;
     std::vector<std::pair<int64_t, WorkItem>> v;
     // items are ranges of units: rows, or row segments of long rows (unit u = row u / nseg,
     // segment u % nseg)
@@ -525,16 +577,31 @@ static std::vector<WorkItem> make_items(const std::vector<GridDesc> &grids, int 
         if (!whole) {
             const double share = (double)units / (double)std::max<int64_t>(total_units, 1);
             chunks = (int)std::ceil(share * target_items / ntiles);
-            // no item smaller than 8x its histogram flush (T x Dt entries): units * length >= 8 T
-            const int min_units = (int)std::min<int64_t>(units, (8ll * T + ul - 1) / std::max(1, ul));
+            // no item smaller than 8x its histogram flush (HR x Dt entries): units * length >= 8 HR
+            const int min_units = (int)std::min<int64_t>(units, (8ll * HR + ul - 1) / std::max(1, ul));
             chunks = std::min(chunks, std::max(1, units / std::max(1, min_units)));
             chunks = std::max(chunks, (units + max_units - 1) / max_units);
             chunks = std::max(1, std::min(chunks, units));
+            if (grids.size() == 1) {
+                // one complex: the chunk count whose items fill the CTAs' rounds best (makespan
+                // ceil(items / target) / chunks), fewest chunks on ties
+                const int lo_c = std::max(1, (units + max_units - 1) / max_units);
+                const int hi_c = std::max(lo_c, std::min(units, units / std::max(1, min_units)));
+                double best = 1e30;
+                for (int c2 = lo_c; c2 <= std::min(hi_c, lo_c + 4 * std::max(1, target_items)); ++c2) {
+                    const int64_t items_n = (int64_t)ntiles * c2;
+                    const double span = (double)((items_n + target_items - 1) / std::max(1, target_items)) / c2;
+                    if (span < best - 1e-12) {
+                        best = span;
+                        chunks = c2;
+                    }
+                }
+            }
         }
         const int per = (units + chunks - 1) / chunks;
         for (int t = 0; t < ntiles; ++t)
             for (int r0 = 0; r0 < units; r0 += per) {
-                WorkItem w{c, t, r0, std::min(units, r0 + per)};
+                WorkItem w{c, t % ((d + Dt - 1) / Dt), r0, std::min(units, r0 + per), t / ((d + Dt - 1) / Dt)};
                 v.push_back({(int64_t)(w.r1 - w.r0) * ul, w});
             }
     }
@@ -591,6 +658,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.threads = sh.threads;
     a.L0s = sh.L0s;
     a.segmented = L.segmented ? 1 : 0;
+    a.Tt = sh.Tt;
     const int grid = std::max(1, std::min(sh.grid, n_items));
     {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1032,10 +1100,10 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
     wect_status s = ensure_common_ws(c->ws, T, d);
     if (s) return s;
     const bool direct = false;
-    auto key = std::make_tuple(d, T, sh.Dt, sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1), sh.grid);
+    auto key = std::make_tuple(d, T, sh.Dt, sh.run ? 100 : sh.dpl * (sh.gh ? -1 : 1) + sh.Tt * 100000, sh.grid);
     if (c->ws.items_key != key) {   // (items do not depend on the TMA staging)
         std::vector<GridDesc> gv(1, gd);
-        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, T, c->kflush, sh.grid, false);
+        std::vector<WorkItem> items = make_items(gv, d, sh.Dt, T, c->kflush, sh.grid, false, sh.Tt);
         if ((s = upload_items(c->ws, items, st))) return s;
         c->ws.items_key = key;
     }
@@ -1604,7 +1672,9 @@ static bool batch_shape(wect_batch b, int d, int T, double span, CubShape &sh)
 // Tile-shape code for cache keys: dpl, negative for the global-histogram variant, 100 for runs.
 static int shape_code(const CubShape &sh)
 {
-    return sh.run ? 100 : (sh.dpl * (sh.gh ? -1 : 1) + (sh.threads == 256 ? 1000 : 0) + (sh.L0s > 0 ? 10000 : 0));
+    return sh.run ? 100
+                  : (sh.dpl * (sh.gh ? -1 : 1) + (sh.threads == 256 ? 1000 : 0) + (sh.L0s > 0 ? 10000 : 0) +
+                     sh.Tt * 100000);
 }
 
 // Work items of a batch for a tile shape.  Whole-complex items (scanned in the CTA, stored
@@ -1614,10 +1684,10 @@ static wect_status batch_items(wect_batch b, int d, int T, const CubShape &sh, b
     int64_t maxnv = 0;
     for (auto &g : b->h_grids) maxnv = std::max<int64_t>(maxnv, g.nv);
     const int ntiles = (d + sh.Dt - 1) / sh.Dt;
-    direct = !sh.gh && maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
+    direct = !sh.gh && sh.Tt == 0 && maxnv <= b->kflush && (int64_t)b->count * ntiles >= 2 * (int64_t)sh.grid;
     auto key = std::make_tuple(d, T, sh.Dt, shape_code(sh), direct ? 1 : 0);
     if (b->ws.items_key == key) return WECT_OK;
-    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, T, b->kflush, 4 * sh.grid, direct);
+    std::vector<WorkItem> items = make_items(b->h_grids, d, sh.Dt, T, b->kflush, 4 * sh.grid, direct, sh.Tt);
     wect_status s = upload_items(b->ws, items, st);
     if (s) return s;
     b->ws.items_key = key;
@@ -1711,7 +1781,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         starts.assign(b->count + 1, 0);
         for (int i = 0; i < b->count; ++i) {
             std::vector<GridDesc> one(1, b->h_grids[i]);
-            std::vector<WorkItem> it = make_items(one, d, sh.Dt, T, b->kflush, sh.grid, false);
+            std::vector<WorkItem> it = make_items(one, d, sh.Dt, T, b->kflush, sh.grid, false, sh.Tt);
             for (auto &w : it) w.cx = i;
             starts[i] = (int)all.size();
             all.insert(all.end(), it.begin(), it.end());
@@ -1747,6 +1817,7 @@ extern "C" wect_status wect_batch_compute_loop(wect_batch b, const double *dirs,
         a.threads = sh.threads;
         a.L0s = sh.L0s;
         a.segmented = b->h_grids[i].nseg > 1 ? 1 : 0;
+        a.Tt = sh.Tt;
         const int grid = std::max(1, std::min(sh.grid, a.n_items));
         KL(sh.run ? launch_cubical_run(b->n, a, grid, sh.smem, st)
                   : launch_cubical_fwd(b->n, b->nsplit, sh.dpl, sh.gh, a, grid, sh.smem, st),

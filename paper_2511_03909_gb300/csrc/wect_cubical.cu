@@ -34,8 +34,35 @@ namespace wect {
 
 constexpr int kFwdThreads = 512;
 
+// Work item the CTA is on (its threshold tile is read back by the rare fix-ups, so that the hot
+// row loop keeps no tile registers).
+__shared__ int s_fwd_item;
+
+// Threshold tile of the CTA's current item: the shared histogram's row of bin b is
+// clamp(b - base, 0, HR - 1), and rows [rlo, rhi) carry the tile's bins (row 0 below and row
+// HR - 1 above are discard rows, except at the ends of the range where they are the first and
+// last bins).  Untiled: base 0, HR = T, rows [0, T).
+__device__ __forceinline__ void fwd_tile(const CubicalFwdArgs &P, int &base, int &HR, int &rlo, int &rhi)
+{
+    const int T = P.T;
+    base = 0;
+    HR = T;
+    rlo = 0;
+    rhi = T;
+    if (P.Tt > 0) {
+        const int tt = P.items[s_fwd_item].tt;
+        const int q0 = tt * P.Tt, q1 = min(T, q0 + P.Tt);
+        base = (tt == 0) ? 0 : q0 - 1;
+        rlo = q0 - base;
+        rhi = q1 - base;
+        HR = (q1 < T) ? rhi + 1 : rhi;
+    }
+}
+
 // The float32 filter could not decide the bin of vertex (i0,i1,i2) in direction p: evaluate the
 // float64 height, find its exact bin and move the contribution if the tentative bin was wrong.
+// nr is the row filter's (real) integer offset; the histogram rows are those of the item's
+// threshold tile (fwd_tile).
 template <int N, int NSPLIT, bool GH>
 __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDesc &g, int p, int i0, int i1, int i2,
                                            int thi, int nr, int col, uint32_t histAddr, int Dt, uint32_t HOFF,
@@ -55,8 +82,12 @@ __device__ __noinline__ void cubical_fixup(const CubicalFwdArgs &P, const GridDe
         }
         return;
     }
-    const uint32_t at = histAddr + ((uint32_t)bt * (uint32_t)Dt + (uint32_t)col) * 4u;
-    const uint32_t ae = histAddr + ((uint32_t)be * (uint32_t)Dt + (uint32_t)col) * 4u;
+    int base, HR, rlo, rhi;
+    fwd_tile(P, base, HR, rlo, rhi);
+    const int rt = min(max(bt - base, 0), HR - 1), re = min(max(be - base, 0), HR - 1);
+    if (rt == re) return;           // both in one discard row of the tile
+    const uint32_t at = histAddr + ((uint32_t)rt * (uint32_t)Dt + (uint32_t)col) * 4u;
+    const uint32_t ae = histAddr + ((uint32_t)re * (uint32_t)Dt + (uint32_t)col) * 4u;
     if (NSPLIT == 1) {
         red_shared_add(at, -cv);
         red_shared_add(ae, cv);
@@ -117,13 +148,15 @@ __device__ __noinline__ void cubical_fixup_block(const CubicalFwdArgs &P, const 
 // One unit of a grid row (the whole row, or L0 vertices of it from x0 on when long rows are walked
 // in segments; Lfull is the row's length) for the DPL directions of each lane.  CLAMP selects the
 // variant whose bins may leave [0, T-1] (heights outside the threshold range); the other variant
-// has been proven in range for the whole row and skips the clamp.
-template <int N, int NSPLIT, int DPL, bool CLAMP, bool GH>
+// has been proven in range for the whole row and skips the clamp.  rf[j].nr arrives shifted by the
+// item's threshold-tile base, so that thi + nr - kMagicBits is the histogram row, clamped to
+// [0, HR - 1] (untiled: base 0, HR = T; the non-GEN instances are never tiled and take T).
+template <int N, int NSPLIT, int DPL, bool CLAMP, bool GH, bool GEN>
 __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc &g, const int32_t *crow, int CP, int L0,
                                         int x0, int Lfull, int i1, int i2, const float (&S0)[DPL], const RowFilter (&rf)[DPL],
                                         const int (&oct)[DPL], const int (&col)[DPL], int pbase, uint32_t histAddr,
                                         int Dt, uint32_t HOFF, const DirFilter *dirf, int colbase, uint32_t *wq,
-                                        unsigned long long *const (&orow)[DPL], unsigned long long *oc)
+                                        unsigned long long *const (&orow)[DPL], unsigned long long *oc, int HR)
 {
     constexpr int NOCT = 1 << N;
     constexpr int U = (NSPLIT == 1 && DPL <= 2) ? 8 : 4;
@@ -198,7 +231,7 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
                 if (!CLAMP) {
                     addr = (uint32_t)thi[j] * D4 + hb[j];
                 } else {
-                    const int b = clamp_bin(thi[j], rf[j].nr, T);
+                    const int b = clamp_bin(thi[j], rf[j].nr, GEN ? HR : T);
                     addr = hb[j] + (uint32_t)b * D4;
                 }
                 if (NSPLIT == 1) {
@@ -233,10 +266,10 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             const int hvs = (NSPLIT == 2) ? crow[NOCT * CP + oct[j] * CP + i0] : 0;
             int tlo, thi;
             filter_ceil(k0, S0[j], rf[j].Glo, rf[j].Ghi, tlo, thi);
-            const int b = clamp_bin(thi, rf[j].nr, T);
             if constexpr (GH) {
-                if (orow[j]) atomicAdd(orow[j] + b, (unsigned long long)(long long)cvs);
+                if (orow[j]) atomicAdd(orow[j] + clamp_bin(thi, rf[j].nr, T), (unsigned long long)(long long)cvs);
             } else {
+                const int b = clamp_bin(thi, rf[j].nr, GEN ? HR : T);
                 const uint32_t addr = histAddr + ((uint32_t)b * (uint32_t)Dt + (uint32_t)col[j]) * 4u;
                 if (NSPLIT == 1) {
                     red_shared_add(addr, cvs);
@@ -247,8 +280,10 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
             }
             if (tlo != thi) {
                 const int p = (pbase + col[j] < P.d) ? P.perm[pbase + col[j]] : P.d;
-                cubical_fixup<N, NSPLIT, GH>(P, g, p, x0 + i0, i1, i2, thi, rf[j].nr, col[j], histAddr, Dt, HOFF, cvs, hvs,
-                                             oc);
+                int tb = 0, thr, t1, t2;                      // the real row offset: rf[j].nr + base
+                if (GEN) fwd_tile(P, tb, thr, t1, t2);
+                cubical_fixup<N, NSPLIT, GH>(P, g, p, x0 + i0, i1, i2, thi, rf[j].nr + tb, col[j], histAddr, Dt, HOFF,
+                                             cvs, hvs, oc);
             }
         }
         k0 += 2.0f;
@@ -257,23 +292,26 @@ __device__ __forceinline__ void fwd_row(const CubicalFwdArgs &P, const GridDesc 
 
 // ------------------------------------------------------------------ forward
 
-template <int N, int NSPLIT, int DPL, bool GH, bool SEG>
+// GEN instances walk long rows in segments and threshold tiles; the others (whole rows, all T
+// rows in the histogram) keep the row loop free of both.
+template <int N, int NSPLIT, int DPL, bool GH, bool GEN>
 __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const CubicalFwdArgs P)
 {
     constexpr int NOCT = 1 << N;
     constexpr int NROWS = (N >= 3) ? 9 : (N == 2 ? 3 : 1);      // neighbouring rows of a box
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
     __shared__ __align__(8) unsigned long long s_mbar[16][2];    // TMA completion, per row group
     const int T = P.T, Dt = P.Dt, CP = P.CP;
-    const int histWords = GH ? 0 : T * Dt;      // GH: no shared histogram
+    // histogram rows: T, or a threshold tile of Tt bins and a discard row on each side
+    const int HRmax = (GEN && P.Tt > 0) ? P.Tt + 2 : T;
+    const int histWords = GH ? 0 : HRmax * Dt;  // GH: no shared histogram
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int WC = Dt / (32 * DPL);         // warps across the direction tile = warps of a row group
     const int RG = nwarps / WC;             // row groups, each walking its own rows
     const int wcol = wid % WC, rgroup = wid / WC;
     const int gtid = wcol * 32 + lane, gthreads = WC * 32;
-    int32_t *hist = reinterpret_cast<int32_t *>(smem);                          // NSPLIT planes [T][Dt]
+    int32_t *hist = reinterpret_cast<int32_t *>(smem);                          // NSPLIT planes [HRmax][Dt]
     DirFilter *dirf = reinterpret_cast<DirFilter *>(hist + NSPLIT * histWords);  // [Dt]
     const int rowbuf = NSPLIT * NOCT * CP;                                       // words of one row buffer
     const int nbuf = (WC == 1) ? 1 : 2;     // a one-warp group needs no second buffer (warp-synchronous)
@@ -302,14 +340,19 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = atomicAdd(P.counter, 1);
+        if (tid == 0) s_fwd_item = atomicAdd(P.counter, 1);
         __syncthreads();
-        const int it = s_item;
+        const int it = s_fwd_item;
         if (it >= P.n_items) break;
         const WorkItem W = P.items[it];
         const GridDesc g = P.grids[W.cx];
         const int L0 = g.L[0], L1 = g.L[1];
         const int pbase = W.dtile * Dt;
+        // threshold tile of the item: the histogram row of bin b is clamp(b - base, 0, HR - 1), and
+        // rows [rlo, rhi) carry the tile's bins (row 0 below and row HR - 1 above are discard
+        // rows except at the ends of the range, where they are the first and last bins)
+        int base = 0, HR = T, rlo = 0, rhi = T;
+        if (GEN) fwd_tile(P, base, HR, rlo, rhi);
 
         // ---- float32 filter constants of the tile's directions, one per column
         for (int c = tid; c < Dt; c += blockDim.x) {
@@ -345,7 +388,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         // ---- each row group walks rows r0 + rgroup, r0 + rgroup + RG, ... with a double-buffered
         // row of octant contributions (one group barrier per row, no block-wide barrier)
         // (a grid walked in segments is never staged: its box would not fit the stage)
-        const bool tma = (N >= 2) && P.L0s > 0 && g.tmap != nullptr && (!SEG || g.nseg == 1);
+        const bool tma = (N >= 2) && P.L0s > 0 && g.tmap != nullptr && (!GEN || g.nseg == 1);
         const uint32_t boxBytes = (uint32_t)(NROWS * L0) * 4u;
         // box of the rows around row r' (rows outside the grid come back as zeros)
         auto stage_row = [&](int rr, unsigned kb) {
@@ -359,9 +402,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         for (int r = W.r0 + rgroup; r < W.r1; r += RG, parity ^= 1) {
             int32_t *crow = cgrp + (nbuf == 2 ? parity : 0) * rowbuf;
             if (nbuf == 1) __syncwarp();        // the previous row's reads are done before the rewrite
-            // unit r: grid row rr, or (SEG instances only) its segment of Lu vertices from x0 when
+            // unit r: grid row rr, or (GEN instances only) its segment of Lu vertices from x0 when
             // the grid's rows are walked in segments (such grids are not TMA-staged)
-            const bool segd = SEG && g.nseg > 1;
+            const bool segd = GEN && g.nseg > 1;
             const int rr = segd ? r / g.nseg : r;
             const int x0 = segd ? (r - rr * g.nseg) * g.seg : 0;
             const int Lu = segd ? min(g.seg, L0 - x0) : L0;
@@ -405,22 +448,23 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
                 S0[j] = f.S0;
                 oct[j] = f.oct;
                 rf[j] = make_row_filter<N>(f, i1, i2, g.L);
-                // all bins of the row provably inside [0, T-1]?  (NaN/inf compare false)
+                if (GEN) rf[j].nr -= base;          // histogram rows of the item's threshold tile
+                // all rows of the row provably inside [0, HR-1]?  (NaN/inf compare false)
                 const float A = __fmul_ru((float)(L0 - 1), fabsf(f.S0));
                 const float lowf = __fadd_rd(__fsub_rd(rf[j].Glo, A), (float)(rf[j].nr - 1));
                 const float highf = __fadd_ru(__fadd_ru(rf[j].Ghi, A), (float)(rf[j].nr + 1));
-                clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(T - 1));
+                clampRow |= !(lowf >= 0.0f) || !(highf <= (float)(HR - 1));
             }
             if constexpr (GH) {
-                fwd_row<N, NSPLIT, DPL, true, true>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
-                                                    HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+                fwd_row<N, NSPLIT, DPL, true, true, GEN>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                                                    HOFF, dirf, wcol * 32 * DPL, wq, orow, oc, HR);
             } else {
                 if (__any_sync(0xffffffffu, clampRow))
-                    fwd_row<N, NSPLIT, DPL, true, false>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
-                                                         HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+                    fwd_row<N, NSPLIT, DPL, true, false, GEN>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr, Dt,
+                                                         HOFF, dirf, wcol * 32 * DPL, wq, orow, oc, HR);
                 else
-                    fwd_row<N, NSPLIT, DPL, false, false>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
-                                                          Dt, HOFF, dirf, wcol * 32 * DPL, wq, orow, oc);
+                    fwd_row<N, NSPLIT, DPL, false, false, GEN>(P, g, crow, CP, Lu, x0, L0, i1, i2, S0, rf, oct, col, pbase, histAddr,
+                                                          Dt, HOFF, dirf, wcol * 32 * DPL, wq, orow, oc, HR);
             }
         }
         __syncthreads();
@@ -428,7 +472,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
             if (P.direct)
                 cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
             else
-                cubical_flush<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
+                cubical_flush<NSPLIT>(hist, HRmax, rlo, rhi, base, T, Dt, W.dtile, P.d, P.perm, oc);
         }
     }
 }
@@ -455,24 +499,24 @@ __global__ void grid_max_abs_kernel(const GridDesc *grids, const double *dirs, i
 
 // The dynamic shared-memory opt-in is set once per kernel instance and size (never inside a
 // stream capture once a size has been seen).
-template <int N, int NSPLIT, int DPL, bool GH, bool SEG>
+template <int N, int NSPLIT, int DPL, bool GH, bool GEN>
 static cudaError_t launch_fwd_s(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
 {
     static size_t done = 0;
     if (smem > done) {
-        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL, GH, SEG>,
+        cudaError_t e = cudaFuncSetAttribute(cubical_fwd_kernel<N, NSPLIT, DPL, GH, GEN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         done = smem;
     }
     if (!launch) return cudaSuccess;
     const int threads = (a.threads > 0 && a.threads <= kFwdThreads) ? a.threads : kFwdThreads;
-    cubical_fwd_kernel<N, NSPLIT, DPL, GH, SEG><<<grid, threads, smem, st>>>(a);
+    cubical_fwd_kernel<N, NSPLIT, DPL, GH, GEN><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-// The instance that walks segments of long rows only when some grid of the launch needs it (the
-// other keeps the row loop free of the unit decoding); preparing sets up both.
+// The general instance (segments of long rows, threshold tiles) only when the launch needs it;
+// preparing sets up both.
 template <int N, int NSPLIT, int DPL, bool GH>
 static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, cudaStream_t st, bool launch)
 {
@@ -480,8 +524,8 @@ static cudaError_t launch_fwd_t(const CubicalFwdArgs &a, int grid, size_t smem, 
         cudaError_t e = launch_fwd_s<N, NSPLIT, DPL, GH, false>(a, grid, smem, st, false);
         return e != cudaSuccess ? e : launch_fwd_s<N, NSPLIT, DPL, GH, true>(a, grid, smem, st, false);
     }
-    return a.segmented ? launch_fwd_s<N, NSPLIT, DPL, GH, true>(a, grid, smem, st, true)
-                       : launch_fwd_s<N, NSPLIT, DPL, GH, false>(a, grid, smem, st, true);
+    return (a.segmented || a.Tt > 0) ? launch_fwd_s<N, NSPLIT, DPL, GH, true>(a, grid, smem, st, true)
+                                     : launch_fwd_s<N, NSPLIT, DPL, GH, false>(a, grid, smem, st, true);
 }
 
 template <int N, int NSPLIT>

@@ -106,18 +106,21 @@ __device__ __forceinline__ void octant_contribs_box(const int32_t *box, const Gr
 
 // ------------------------------------------------------------------ forward helpers
 
-// Add the CTA's partial histograms into the int64 output block [d][T] and clear them.
+// Add the CTA's partial histograms into the int64 output block [d][T] and clear them.  The
+// histogram has HR rows (the plane stride of the two-plane form); rows [rlo, rhi) hold the bins
+// base + rlo .. base + rhi - 1 of the item's threshold tile, the others are discard rows (untiled:
+// HR = T, rows [0, T), base 0).
 template <int NSPLIT>
-__device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int dtile, int d, const int *perm,
-                                              unsigned long long *out)
+__device__ __forceinline__ void cubical_flush(int32_t *hist, int HR, int rlo, int rhi, int base, int T, int Dt,
+                                              int dtile, int d, const int *perm, unsigned long long *out)
 {
-    const int hw = T * Dt;
+    const int hw = HR * Dt;
     if (blockDim.x % Dt == 0) {
         // each thread keeps one column: no division and one perm load per thread
         const int col = threadIdx.x % Dt, bstep = blockDim.x / Dt;
         const int p = (dtile * Dt + col < d) ? perm[dtile * Dt + col] : d;
-        unsigned long long *orow = out + (int64_t)min(p, d - 1) * T;
-        for (int b = threadIdx.x / Dt; b < T; b += bstep) {
+        unsigned long long *orow = out + (int64_t)min(p, d - 1) * T + base;
+        for (int b = threadIdx.x / Dt; b < HR; b += bstep) {
             const int idx = b * Dt + col;
             int64_t v;
             if (NSPLIT == 1) {
@@ -127,7 +130,7 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int 
                 hist[hw + idx] = 0;
             }
             hist[idx] = 0;
-            if (p < d && v != 0) atomicAdd(orow + b, (unsigned long long)v);
+            if (p < d && v != 0 && b >= rlo && b < rhi) atomicAdd(orow + b, (unsigned long long)v);
         }
         return;
     }
@@ -142,7 +145,7 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int T, int Dt, int 
             hist[hw + idx] = 0;
         }
         hist[idx] = 0;
-        if (p < d && v != 0) atomicAdd(out + (int64_t)p * T + b, (unsigned long long)v);
+        if (p < d && v != 0 && b >= rlo && b < rhi) atomicAdd(out + (int64_t)p * T + base + b, (unsigned long long)v);
     }
 }
 

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) cubical_run_kernel(const Cubic
         if (P.direct)
             cubical_flush_direct<1>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
         else
-            cubical_flush<1>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
+            cubical_flush<1>(hist, T, 0, T, 0, T, Dt, W.dtile, P.d, P.perm, oc);
     }
 }
 

@@ -49,11 +49,13 @@ struct GridDesc {
     int nseg = 1;
 };
 
-// A unit of work of the cubical kernels: one complex, one direction tile, a row range.
+// A unit of work of the cubical kernels: one complex, one direction tile, a row range (units of
+// rows or row segments), and for the forward stencil kernel a threshold tile (0 when untiled).
 struct WorkItem {
     int cx;
     int dtile;
     int r0, r1;
+    int tt = 0;
 };
 
 // ------------------------------------------------------------------ float64 exact path

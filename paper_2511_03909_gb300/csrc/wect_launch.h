@@ -28,6 +28,8 @@ struct CubicalFwdArgs {
     int L0s;                      // > 0: rows are staged by TMA from grids with a tensor map, into
                                   // per-row-group buffers of 2 x 3^(n-1) rows of L0s int32
     int segmented;                // some grid walks its rows in segments (GridDesc::seg, nseg)
+    int Tt;                       // > 0: threshold tiles of Tt bins (WorkItem::tt); the shared
+                                  // histogram then holds Tt + 2 rows (a discard row on each side)
 };
 
 struct CubicalBwdArgs {
