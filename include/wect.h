@@ -294,8 +294,10 @@ WECT_API wect_status wect_batch_backward_f64(wect_batch b, const double *dirs, i
  * Time the candidate tile shapes for (d, T) on this batch (synchronises) and keep the fastest:
  * for the per-vertex stencil kernel every tile width Dt (32 .. 32 x directions per lane x warps),
  * 1, 2 or 4 directions per lane, and CTAs of 512 or 256 threads; for the run-based kernel (one
- * histogram plane) Dt = 32 .. 256.  When no shape holds all T thresholds in shared memory, the
- * threshold-tiled default shape stays.  wect_batch_tuned_shape reports the choice.
+ * histogram plane) Dt = 32 .. 256.  A per-vertex candidate whose histogram cannot hold all T
+ * thresholds runs in threshold tiles (the largest band of bins that fits beside its row
+ * buffers), so the tuner also chooses the threshold tile.  wect_batch_tuned_shape reports the
+ * choice (the threshold tile follows from the direction tile).
  */
 WECT_API wect_status wect_batch_autotune(wect_batch b, const double *dirs, int d, int T, double lo, double hi,
                                 int64_t *scratch_out, wect_stream stream);

@@ -464,8 +464,7 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
         }
         if (Dt_req > 0) break;
     }
-    if (dpl_req > 0 || Dt_req > 0) return false;
-    // no shared histogram of all T rows fits: threshold tiles of Tt bins (plus a discard row on
+    // no shared histogram of all T rows fits (for a pinned tile shape: that one): threshold tiles of Tt bins (plus a discard row on
     // each side), one pass over the grid per (direction tile, threshold tile).  A pass costs a
     // per-vertex part (octant contributions, row set-up) and a per-update part; measured on the
     // 128^3 volume (T = 128, 512, 1024 at tile widths 256, 64, 32) they weigh about 45 : 1 per
@@ -474,8 +473,9 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
     {
         int64_t bestCost = INT64_MAX;
         CubShape best;
-        for (int Dt = Dmax; Dt >= 32; Dt /= 2)
+        for (int Dt = (Dt_req > 0 ? Dt_req : Dmax); Dt >= 32; Dt /= 2)
             for (int dpl : {2, 4, 1}) {
+                if ((Dt_req > 0 && Dt != Dt_req) || (dpl_req > 0 && dpl != dpl_req)) continue;
                 if (Dt % (32 * dpl)) continue;
                 const int WC = Dt / (32 * dpl);
                 if (WC > warps || warps % WC) continue;
@@ -512,6 +512,7 @@ static bool cub_shape(int n, int nsplit, int d, int T, int maxL0, CubShape &out,
             return true;
         }
     }
+    if (dpl_req > 0 || Dt_req > 0) return false;
     // not even threshold tiles fit: scatter into the global int64 difference table instead
     const int Dt = std::min(Dmax, 256);
     out.dpl = Dt >= 64 ? 2 : 1;
