@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
             if (P.direct)
                 cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
             else
-                cubical_flush<NSPLIT>(hist, HRmax, rlo, rhi, base, T, Dt, W.dtile, P.d, P.perm, oc);
+                cubical_flush<NSPLIT, GEN>(hist, HRmax, rlo, rhi, base, T, Dt, W.dtile, P.d, P.perm, oc);
         }
     }
 }

@@ -109,8 +109,8 @@ __device__ __forceinline__ void octant_contribs_box(const int32_t *box, const Gr
 // Add the CTA's partial histograms into the int64 output block [d][T] and clear them.  The
 // histogram has HR rows (the plane stride of the two-plane form); rows [rlo, rhi) hold the bins
 // base + rlo .. base + rhi - 1 of the item's threshold tile, the others are discard rows (untiled:
-// HR = T, rows [0, T), base 0).
-template <int NSPLIT>
+// HR = T, rows [0, T), base 0; only TILED instances check the row range).
+template <int NSPLIT, bool TILED = false>
 __device__ __forceinline__ void cubical_flush(int32_t *hist, int HR, int rlo, int rhi, int base, int T, int Dt,
                                               int dtile, int d, const int *perm, unsigned long long *out)
 {
@@ -130,7 +130,7 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int HR, int rlo, in
                 hist[hw + idx] = 0;
             }
             hist[idx] = 0;
-            if (p < d && v != 0 && b >= rlo && b < rhi) atomicAdd(orow + b, (unsigned long long)v);
+            if (p < d && v != 0 && (!TILED || (b >= rlo && b < rhi))) atomicAdd(orow + b, (unsigned long long)v);
         }
         return;
     }
@@ -145,7 +145,8 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int HR, int rlo, in
             hist[hw + idx] = 0;
         }
         hist[idx] = 0;
-        if (p < d && v != 0 && b >= rlo && b < rhi) atomicAdd(out + (int64_t)p * T + base + b, (unsigned long long)v);
+        if (p < d && v != 0 && (!TILED || (b >= rlo && b < rhi)))
+            atomicAdd(out + (int64_t)p * T + base + b, (unsigned long long)v);
     }
 }
 
