@@ -335,6 +335,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
         mbar_fence_init();
     }
     unsigned krow = 0;                      // rows this group has staged (buffer krow & 1, phase krow >> 1)
+    // the flush's transpose tiles: the shared memory past the histogram (direction filters, row
+    // buffers, fix-up queues, staging boxes), idle between items
+    const int flushTiles = (int)((dynamic_smem_bytes() - (uint32_t)(NSPLIT * histWords) * 4u) / (NSPLIT * 32u * 33u * 4u));
 
     for (int i = tid; i < NSPLIT * histWords; i += blockDim.x) hist[i] = 0;
 
@@ -472,7 +475,8 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
             if (P.direct)
                 cubical_flush_direct<NSPLIT>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
             else
-                cubical_flush<NSPLIT, GEN>(hist, HRmax, rlo, rhi, base, T, Dt, W.dtile, P.d, P.perm, oc);
+                cubical_flush_coalesced<NSPLIT, GEN>(hist, HRmax, rlo, rhi, base, T, Dt, W.dtile, P.d, P.perm, oc,
+                                                     hist + NSPLIT * histWords, flushTiles);
         }
     }
 }

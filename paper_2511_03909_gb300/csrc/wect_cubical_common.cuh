@@ -150,6 +150,60 @@ __device__ __forceinline__ void cubical_flush(int32_t *hist, int HR, int rlo, in
     }
 }
 
+// The same flush with coalesced global atomics.  cubical_flush's warps add 32 directions of one
+// bin, 32 rows of the output apart; here each warp moves a 32 x 32 block (32 bins x 32 columns)
+// through a padded tile of its own in shared memory (conflict-free on both sides) and adds each
+// column's 32 bins as one run of 32 consecutive int64, a quarter of the L2 sectors.  scratch
+// holds ntiles tiles of NSPLIT x 32 x 33 words (the CTA's shared memory past the histogram, idle
+// between items); warps beyond ntiles stay idle, and with no tile at all cubical_flush runs.  Dt
+// is a multiple of 32.
+template <int NSPLIT, bool TILED = false>
+__device__ __forceinline__ void cubical_flush_coalesced(int32_t *hist, int HR, int rlo, int rhi, int base, int T,
+                                                        int Dt, int dtile, int d, const int *perm,
+                                                        unsigned long long *out, int32_t *scratch, int ntiles)
+{
+    if (ntiles <= 0) {
+        cubical_flush<NSPLIT, TILED>(hist, HR, rlo, rhi, base, T, Dt, dtile, d, perm, out);
+        return;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = min((int)(blockDim.x >> 5), ntiles);
+    const int hw = HR * Dt, ncb = Dt >> 5, nblk = ncb * ((HR + 31) >> 5);
+    if (wid < nw) {
+        int32_t *sc = scratch + wid * (NSPLIT * 32 * 33);
+        for (int blk = wid; blk < nblk; blk += nw) {
+            const int cb = blk % ncb, rb = blk / ncb;
+            const int c0 = cb * 32, b0 = rb * 32;
+            // bins b0 + k, columns c0 + lane: row reads, cleared, into the tile's rows
+            for (int k = 0; k < 32 && b0 + k < HR; ++k) {
+                const int idx = (b0 + k) * Dt + c0 + lane;
+                sc[k * 33 + lane] = hist[idx];
+                hist[idx] = 0;
+                if (NSPLIT == 2) {
+                    sc[32 * 33 + k * 33 + lane] = hist[hw + idx];
+                    hist[hw + idx] = 0;
+                }
+            }
+            __syncwarp();
+            // column c0 + k, bins b0 + lane: one run of 32 consecutive int64 of direction perm[c0 + k]
+            const int pl = (dtile * Dt + c0 + lane < d) ? perm[dtile * Dt + c0 + lane] : d;
+            const int b = b0 + lane;
+            const bool rowok = b < HR && (!TILED || (b >= rlo && b < rhi));
+            for (int k = 0; k < 32; ++k) {
+                const int p = __shfl_sync(0xffffffffu, pl, k);
+                int64_t v = 0;
+                if (rowok) {
+                    v = sc[lane * 33 + k];
+                    if (NSPLIT == 2) v = ((int64_t)sc[32 * 33 + lane * 33 + k] << 16) + (int64_t)(uint32_t)v;
+                }
+                if (p < d && v != 0) atomicAdd(out + (int64_t)p * T + base + b, (unsigned long long)v);
+            }
+            __syncwarp();
+        }
+        fence_proxy_async_smem();           // the tiles may be TMA staging space of the next item
+    }
+}
+
 // The item covered every row of its complex: the histogram is the complete difference table of
 // its directions.  Scan it over the thresholds (Algorithm 1's cumulative sum) and store the
 // transform directly (no atomics, no separate scan).

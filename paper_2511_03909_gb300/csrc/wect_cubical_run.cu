@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(kRunThreads, 1) cubical_run_kernel(const Cubic
     const uint32_t D4 = (uint32_t)Dt * 4u;
     const double lo = P.range[0], hi = P.range[1], step = P.range[2];
 
+    // the flush's transpose tiles: the shared memory past the histogram, idle between items
+    const int flushTiles = (int)((dynamic_smem_bytes() - (uint32_t)histWords * 4u) / (32u * 33u * 4u));
+
     for (int i = tid; i < histWords; i += blockDim.x) hist[i] = 0;
 
     for (;;) {
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kRunThreads, 1) cubical_run_kernel(const Cubic
         if (P.direct)
             cubical_flush_direct<1>(hist, T, Dt, W.dtile, P.d, P.perm, oc);
         else
-            cubical_flush<1>(hist, T, 0, T, 0, T, Dt, W.dtile, P.d, P.perm, oc);
+            cubical_flush_coalesced<1>(hist, T, 0, T, 0, T, Dt, W.dtile, P.d, P.perm, oc, hist + histWords, flushTiles);
     }
 }
 

@@ -270,6 +270,21 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Bytes of dynamic shared memory the CTA was launched with.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA)
+// accesses of the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void red_shared_add(uint32_t addr, int32_t v)
 {
     asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
