@@ -357,17 +357,25 @@ def run_gpu(args):
         ms = float(t.item())
     value = evals_per_step * ws / (ms / 1e3)
 
-    # ---- end to end through the public API, host buffers, copies inside the timed region
+    # ---- end to end through the public API with host buffers: wect_compute_host reads the
+    # page-locked weights and directions and writes the page-locked table itself, so every
+    # host<->device byte of the step moves inside the timed region
+    def step_host():
+        cx.wect_host(grid_h, dirs_h, T, wl.lo, wl.hi, out=out_h, sync=False)
+
+    for _ in range(3):
+        flush.zero_()
+        step_host()
+    barrier()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.zero_()
         e2e_ev[i][0].record()
-        grid_d.copy_(grid_h, non_blocking=True)
-        dirs_d.copy_(dirs_h, non_blocking=True)
-        step()
-        out_h.copy_(out, non_blocking=True)
+        step_host()
         e2e_ev[i][1].record()
     barrier()
+    assert torch.equal(out_h, out.cpu()), "host entry and device entry disagree"
+
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
     if dist:
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
@@ -443,7 +451,9 @@ def run_gpu(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(grid_h.numel() + dirs_h.numel() * 8),
-                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms,
+                "call": "wect_compute_host with page-locked weights, directions and table (read and written "
+                        "by the library's kernels through their device mapping)"},
         "gpu_launches": int(launches),
         "clocks": ck,
         "wall_s": t_wall,

@@ -173,6 +173,26 @@ WECT_API wect_status wect_compute(wect_complex cx, const double *dirs, int d, in
                          int64_t *out, wect_stream stream);
 
 /*
+ * wect_compute for inputs and output in host memory: optionally new vertex weights, then the
+ * WECT of cx (the same table, bit for bit, as wect_complex_set_weights + wect_compute).
+ *   weights (host)  nv weights of the complex's weight type (as wect_complex_set_weights), or
+ *                   NULL to keep the current weights (ignored for WECT_W_ONE)
+ *   dirs (host)     [d][n] float64
+ *   out (host)      [d][T] int64
+ * Page-locked host buffers (cudaHostAlloc, cudaHostRegister, torch pin_memory) are read and
+ * written by the kernels themselves through their device mapping: the weight conversion reads
+ * the weights, a copy kernel reads the directions, and the final scan writes out.  Pageable
+ * buffers go through cudaMemcpyAsync and device staging kept with the complex (for a pageable
+ * out the call returns after the table has arrived).  Device or managed pointers are also
+ * accepted and used in place.  Asynchronous otherwise: out is complete once the stream reaches
+ * this point, so synchronise the stream before reading it.  Calls on one complex share its
+ * staging: order them on one stream.
+ * Errors: as wect_compute and wect_complex_set_weights.
+ */
+WECT_API wect_status wect_compute_host(wect_complex cx, const void *weights, const double *dirs, int d, int T,
+                                       double lo, double hi, int64_t *out, wect_stream stream);
+
+/*
  * ECF / WECF of cx for one vertex filter f (Eq. "ecf"; Remark "which-ecf": the ECF of an
  * image when f is the pixel intensity and weighted = 0).
  *   filter (dev) [k_0] float64, finite

@@ -76,6 +76,7 @@ def _declare(L):
         "wect_complex_device_status": (_st, [_p, _p]),
         "wect_complex_destroy": (None, [_p]),
         "wect_compute": (_st, [_p, _p, _i, _i, _d, _d, _p, _p]),
+        "wect_compute_host": (_st, [_p, _p, _p, _i, _i, _d, _d, _p, _p]),
         "ecf_compute": (_st, [_p, _p, _i, _d, _d, _i, _p, _p]),
         "wecf_compute": (_st, [_p, _p, _i, _i, _d, _d, _i, _p, _p]),
         "wect_backward": (_st, [_p, _p, _i, _i, _d, _d, _p, _d, _p, _p]),
@@ -115,7 +116,7 @@ def exported_symbols():
         "wect_complex_create_cubical", "wect_complex_create_freudenthal", "wect_complex_create_simplicial",
         "wect_complex_set_weights",
         "wect_complex_num_vertices", "wect_complex_cell_counts", "wect_complex_device_status",
-        "wect_complex_destroy", "wect_compute", "ecf_compute", "wecf_compute", "wect_backward", "wect_backward_f64",
+        "wect_complex_destroy", "wect_compute", "wect_compute_host", "ecf_compute", "wecf_compute", "wect_backward", "wect_backward_f64",
         "wect_batch_create",
         "wect_batch_create_cubical", "wect_batch_set_weights", "wect_batch_count", "wect_batch_total_vertices",
         "wect_batch_compute", "wect_batch_compute_loop", "wect_batch_backward", "wect_batch_backward_f64",
@@ -202,6 +203,7 @@ class _Complex:
     n = 0
     nv = 0
     frac_bits = 0
+    wdtype = None       # torch dtype of the vertex weights (None: unweighted)
 
     def __del__(self):
         if self._h is not None and _lib is not None:
@@ -238,6 +240,32 @@ class _Complex:
             out = torch.empty((d, T), dtype=torch.int64, device=dirs.device)
         _require_cuda(out, "out", torch.int64)
         _check(load().wect_compute(self._h, _ptr(dirs), d, T, lo, hi, _ptr(out), _stream()))
+        return out
+
+    def wect_host(self, weights: torch.Tensor | None, dirs: torch.Tensor, T: int, lo: float = math.nan,
+                  hi: float = math.nan, out: torch.Tensor | None = None, sync: bool = True) -> torch.Tensor:
+        """wect_compute_host: new weights (or None to keep the current ones) and directions from
+        host memory, the [d][T] int64 table into host memory (a page-locked tensor is allocated when
+        out is None).  Page-locked tensors are read and written by the kernels directly.  With
+        sync=False the caller synchronises the current stream before reading out."""
+        for t, name in ((weights, "weights"), (dirs, "dirs"), (out, "out")):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous host tensor")
+        if dirs.dtype != torch.float64 or dirs.dim() != 2 or dirs.shape[1] != self.n:
+            raise ValueError(f"dirs must be float64 [d][{self.n}]")
+        if weights is not None and (weights.numel() != self.nv or
+                                    (self.wdtype is not None and weights.dtype != self.wdtype)):
+            raise ValueError(f"weights must be {self.wdtype} with one value per vertex")
+        d = dirs.shape[0]
+        if out is None:
+            out = torch.empty((d, T), dtype=torch.int64).pin_memory()
+        if out.dtype != torch.int64 or out.numel() != d * T:
+            raise ValueError("out must be int64 [d][T]")
+        _check(load().wect_compute_host(self._h, None if weights is None else C.c_void_p(weights.data_ptr()),
+                                        C.c_void_p(dirs.data_ptr()), d, T, lo, hi, C.c_void_p(out.data_ptr()),
+                                        _stream()))
+        if sync:
+            torch.cuda.current_stream().synchronize()
         return out
 
     def ecf(self, filt: torch.Tensor, T: int, lo: float = math.nan, hi: float = math.nan, weighted: bool = False,
@@ -302,6 +330,7 @@ class CubicalComplex(_Complex):
         if weights is not None:
             _require_cuda(weights, "weights")
             dims = list(reversed(weights.shape))
+            self.wdtype = weights.dtype
         elif dims is None:
             raise ValueError("dims is required for an unweighted grid")
         self.n = len(dims)
@@ -325,6 +354,7 @@ class FreudenthalComplex(_Complex):
         if weights is not None:
             _require_cuda(weights, "weights")
             dims = list(reversed(weights.shape))
+            self.wdtype = weights.dtype
         elif dims is None:
             raise ValueError("dims is required for an unweighted grid")
         self.n = len(dims)
@@ -351,6 +381,7 @@ class SimplicialComplex(_Complex):
         self.frac_bits = int(frac_bits)
         _require_cuda(coords, "coords", torch.float64)
         self.nv, self.n = int(coords.shape[0]), int(coords.shape[1])
+        self.wdtype = None if weights is None else weights.dtype
         self.max_dim = len(simplices)
         counts = (C.c_int64 * (self.max_dim + 1))(self.nv, *[int(s.shape[0]) for s in simplices])
         for i, s in enumerate(simplices):

@@ -202,6 +202,9 @@ struct Workspace {
     DBuf<WorkItem> items;
     DBuf<WorkItem> items_bwd;
     DBuf<int> ranges_bwd;         // per CTA of the octant sums: its first item (and the end)
+    DBuf<double> hdirs;           // wect_compute_host: device copy of the directions
+    DBuf<int64_t> hout;           // wect_compute_host: the difference table before its scan
+    DBuf<unsigned char> hw;       // wect_compute_host: staged pageable weights
     // cache key of the uploaded item list
     std::tuple<int, int, int, int, int> items_key{-1, -1, -1, -1, -1};
     std::tuple<int, int> items_bwd_key{-1, -1};
@@ -210,7 +213,7 @@ struct Workspace {
     {
         range.release(); beta.release(); M.release(); cand.release(); counter.release(); perm.release(); octb.release();
         bins.release(); dtab.release(); S.release(); Rv.release(); Iacc.release(); Gq.release(); gscale.release(); items.release();
-        items_bwd.release(); ranges_bwd.release();
+        items_bwd.release(); ranges_bwd.release(); hdirs.release(); hout.release(); hw.release();
     }
 };
 
@@ -628,7 +631,7 @@ struct CubLaunch {
 // [scan].  items must be uploaded in ws->items already.
 static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, int n_items, bool direct,
                                        const double *dirs, int d, int T, double lo, double hi, bool dflt,
-                                       int64_t out_rows, int64_t *out, cudaStream_t st)
+                                       int64_t out_rows, int64_t *out, cudaStream_t st, int64_t *final_out = nullptr)
 {
     Workspace &ws = *L.ws;
     if (dflt) {
@@ -676,7 +679,10 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
             KL(launch(), "cubical_fwd");
         }
     }
-    if (!direct) KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), out_rows, T, st), "scan_rows");
+    if (!direct)
+        KL(launch_scan_rows_to(reinterpret_cast<unsigned long long *>(out),
+                               reinterpret_cast<unsigned long long *>(final_out ? final_out : out), out_rows, T, st),
+           "scan_rows");
     return WECT_OK;
 }
 
@@ -1046,6 +1052,8 @@ extern "C" wect_status wect_complex_device_status(wect_complex c, wect_stream st
     return status_from_bits(bits);
 }
 
+static wect_status set_weights_locked(wect_complex c, const void *w, cudaStream_t st);
+
 extern "C" wect_status wect_complex_set_weights(wect_complex c, const void *w, wect_stream stream)
 {
     if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
@@ -1053,6 +1061,12 @@ extern "C" wect_status wect_complex_set_weights(wect_complex c, const void *w, w
     if (c->wtype == WECT_W_ONE) return WECT_OK;
     if (!w) return fail(WECT_ERR_INVALID_ARG, "weights is NULL");
     std::lock_guard<std::mutex> lk(c->mu);
+    return set_weights_locked(c, w, st);
+}
+
+// w: device-accessible weights of the complex's type (device memory or mapped pinned host memory)
+static wect_status set_weights_locked(wect_complex c, const void *w, cudaStream_t st)
+{
     if (c->kind == 0) {
         KL(launch_weights_to_w32(c->wtype, w, c->nv, c->frac_bits, c->climit >> c->n, c->d_w32, c->d_status, st),
            "weights_to_w32");
@@ -1084,8 +1098,10 @@ static wect_status dirs_check(wect_complex c, const double *dirs, int d, cudaStr
     return WECT_OK;
 }
 
+// out: the int64 [d][T] table the forward accumulates into; final_out (null: out) receives its
+// scan (simplicial_compute likewise).
 static wect_status cubical_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi, int64_t *out,
-                                   cudaStream_t st)
+                                   cudaStream_t st, int64_t *final_out = nullptr)
 {
     CubShape sh;
     GridDesc gd{};
@@ -1110,7 +1126,8 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
     }
     CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, ul, c->climit, c->d_grid, &c->ws, c->d_status,
                 gd.nseg > 1};
-    return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st);
+    return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st,
+                               final_out);
 }
 
 static wect_status simplicial_range(wect_complex c, const double *dirs, int d, int T, double lo, double hi, cudaStream_t st)
@@ -1130,7 +1147,7 @@ static wect_status simplicial_range(wect_complex c, const double *dirs, int d, i
 }
 
 static wect_status simplicial_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi,
-                                      int64_t *out, cudaStream_t st)
+                                      int64_t *out, cudaStream_t st, int64_t *final_out = nullptr)
 {
     const int Dt = 32;
     const size_t sm = simplex_fwd_smem(c->nsplit, T, Dt);
@@ -1197,7 +1214,9 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
             KL(launch_simplex_fwd(c->nsplit, false, a, std::max(g, 1), st), "simplex_fwd");
         }
     }
-    KL(launch_scan_rows(reinterpret_cast<unsigned long long *>(out), d, T, st), "scan_rows");
+    KL(launch_scan_rows_to(reinterpret_cast<unsigned long long *>(out),
+                           reinterpret_cast<unsigned long long *>(final_out ? final_out : out), d, T, st),
+       "scan_rows");
     return WECT_OK;
 }
 
@@ -1214,6 +1233,69 @@ extern "C" wect_status wect_compute(wect_complex c, const double *dirs, int d, i
     if (c->kind == 0) return cubical_compute(c, dirs, d, T, lo, hi, out, st);   // directions checked in fwd_prep
     if ((s = dirs_check(c, dirs, d, st))) return s;
     return simplicial_compute(c, dirs, d, T, lo, hi, out, st);
+}
+
+// The device address of a caller buffer: device memory of the current device and managed memory
+// as they are, page-locked host memory through its mapping into the device's address space
+// (kernels read and write it over the host link); null for pageable host memory, which is
+// copied instead.
+static void *device_alias(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) return nullptr;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost)
+        return a.devicePointer;
+    return nullptr;
+}
+
+extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, const double *dirs, int d, int T,
+                                         double lo, double hi, int64_t *out, wect_stream stream)
+{
+    if (!c) return fail(WECT_ERR_INVALID_ARG, "NULL complex");
+    if (!dirs || !out) return fail(WECT_ERR_INVALID_ARG, "dirs/out is NULL");
+    if (d < 1) return fail(WECT_ERR_INVALID_ARG, "d must be >= 1");
+    wect_status s = check_range(lo, hi, T);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(c->mu);
+    // the weights: read in place by the conversion kernel, or staged when pageable
+    if (weights && c->wtype != WECT_W_ONE) {
+        const void *wd = device_alias(weights);
+        if (!wd) {
+            const size_t bytes = (size_t)c->nv * c->wbytes;
+            CK(c->ws.hw.ensure(bytes), "alloc weight staging");
+            CK(cudaMemcpyAsync(c->ws.hw.p, weights, bytes, cudaMemcpyHostToDevice, st), "copy weights");
+            wd = c->ws.hw.p;
+        }
+        if ((s = set_weights_locked(c, wd, st))) return s;
+    }
+    // the directions: a device copy (every CTA of the forward reads them)
+    const int64_t nd = (int64_t)d * c->n;
+    CK(c->ws.hdirs.ensure((size_t)nd), "alloc direction copy");
+    const double *dd = static_cast<const double *>(device_alias(dirs));
+    if (dd)
+        KL(launch_copy_f64(dd, c->ws.hdirs.p, nd, st), "copy_f64");
+    else
+        CK(cudaMemcpyAsync(c->ws.hdirs.p, dirs, (size_t)nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy dirs");
+    // the difference table on the device; its scan writes out directly when out is mapped
+    CK(c->ws.hout.ensure((size_t)d * T), "alloc table");
+    int64_t *od = static_cast<int64_t *>(device_alias(out));
+    if (c->kind == 0) {
+        s = cubical_compute(c, c->ws.hdirs.p, d, T, lo, hi, c->ws.hout.p, st, od);
+    } else {
+        if ((s = dirs_check(c, c->ws.hdirs.p, d, st))) return s;
+        s = simplicial_compute(c, c->ws.hdirs.p, d, T, lo, hi, c->ws.hout.p, st, od);
+    }
+    if (s) return s;
+    if (!od)
+        CK(cudaMemcpyAsync(out, c->ws.hout.p, (size_t)d * T * sizeof(int64_t), cudaMemcpyDeviceToHost, st), "copy table");
+    return WECT_OK;
 }
 
 // Algorithm 1 for m caller-supplied vertex filters [m][nv]: exact float64 bins of every filter,

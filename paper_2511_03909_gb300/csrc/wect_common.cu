@@ -124,14 +124,16 @@ __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double 
     }
 }
 
-// In-place inclusive prefix sum of each row of an int64 [rows][T] table (Algorithm 1's final
-// cumulative sum): one warp per row, 32-wide shuffle scans with a running carry.
-__global__ void scan_rows_kernel(unsigned long long *data, int64_t rows, int T)
+// Inclusive prefix sum of each row of an int64 [rows][T] table (Algorithm 1's final cumulative
+// sum) from src into dst (the same table, or another one, e.g. mapped host memory): one warp per
+// row, 32-wide shuffle scans with a running carry.
+__global__ void scan_rows_kernel(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T)
 {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
-    long long *r = reinterpret_cast<long long *>(data) + row * T;
+    const long long *r = reinterpret_cast<const long long *>(src) + row * T;
+    long long *o = reinterpret_cast<long long *>(dst) + row * T;
     long long carry = 0;
     for (int base = 0; base < T; base += 32) {
         const int q = base + lane;
@@ -142,7 +144,7 @@ __global__ void scan_rows_kernel(unsigned long long *data, int64_t rows, int T)
             if (lane >= off) v += u;
         }
         v += carry;
-        if (q < T) r[q] = v;
+        if (q < T) o[q] = v;
         carry = __shfl_sync(0xffffffffu, v, 31);
     }
 }
@@ -151,10 +153,12 @@ __global__ void scan_rows_kernel(unsigned long long *data, int64_t rows, int T)
 // the row, the block scans the piece sums (warp shuffles, then the warp totals), and each thread
 // rewrites its piece as running sums from its exclusive prefix.  A warp per row would walk T / 32
 // dependent steps.
-__global__ void __launch_bounds__(1024) scan_rows_block_kernel(unsigned long long *data, int T)
+__global__ void __launch_bounds__(1024) scan_rows_block_kernel(const unsigned long long *src, unsigned long long *dst,
+                                                               int T)
 {
     __shared__ long long wsum[32];
-    long long *r = reinterpret_cast<long long *>(data) + (int64_t)blockIdx.x * T;
+    const long long *r = reinterpret_cast<const long long *>(src) + (int64_t)blockIdx.x * T;
+    long long *o = reinterpret_cast<long long *>(dst) + (int64_t)blockIdx.x * T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per = (T + blockDim.x - 1) / blockDim.x;
     const int q0 = min(T, (int)threadIdx.x * per), q1 = min(T, q0 + per);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(1024) scan_rows_block_kernel(unsigned long lon
     long long run = v - s + (wid > 0 ? wsum[wid - 1] : 0);   // exclusive prefix of the piece
     for (int q = q0; q < q1; ++q) {
         run += r[q];
-        r[q] = run;
+        o[q] = run;
     }
 }
 
@@ -391,17 +395,37 @@ cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st)
+cudaError_t launch_scan_rows_to(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T,
+                                cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
     if (T >= 1024 && rows <= 65535) {
         // a block of up to 1024 threads per row, about 8 entries per thread
         const int threads = std::min(1024, ((T + 7) / 8 + 31) / 32 * 32);
-        scan_rows_block_kernel<<<(unsigned)rows, threads, 0, st>>>(data, T);
+        scan_rows_block_kernel<<<(unsigned)rows, threads, 0, st>>>(src, dst, T);
         return cudaGetLastError();
     }
     const int wpb = 8;
-    scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(data, rows, T);
+    scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(src, dst, rows, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st)
+{
+    return launch_scan_rows_to(data, data, rows, T, st);
+}
+
+// Copy of n doubles (src: device memory or mapped pinned host memory).
+__global__ void copy_f64_kernel(const double *__restrict__ src, double *__restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_copy_f64(const double *src, double *dst, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    copy_f64_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
 

@@ -191,6 +191,10 @@ cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, 
                             int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
                             int run_order = 0);
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
+// The same scan from src into dst (dst may be mapped pinned host memory; src == dst is in place).
+cudaError_t launch_scan_rows_to(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T,
+                                cudaStream_t st);
+cudaError_t launch_copy_f64(const double *src, double *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
                                cudaStream_t st);
 cudaError_t launch_weights_to_fixed(int wt, const void *w, int64_t nv, int frac_bits, int64_t *out,

@@ -58,4 +58,5 @@ def test_argument_errors_need_no_gpu(lib_path):
     assert L.wect_complex_create_cubical(2, dims, None, 9, 0, None, ctypes.byref(h)) == 1
     assert L.wect_complex_create_cubical(2, dims, None, P.W_F32, 99, None, ctypes.byref(h)) == 1
     assert L.wect_compute(None, None, 1, 8, 0.0, 1.0, None, None) == 1
+    assert L.wect_compute_host(None, None, None, 1, 8, 0.0, 1.0, None, None) == 1
     assert b"NULL" in L.wect_last_error()

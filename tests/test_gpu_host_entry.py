@@ -1,0 +1,95 @@
+"""wect_compute_host: weights and directions from host memory, the table into host memory.
+Page-locked buffers are read and written by the kernels in place, pageable ones are staged; both
+give the oracle's table bit for bit, and the same table as set_weights + wect_compute."""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from gpu_common import SQ2, SQ3, cuda, dev, lib, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    dev()
+    return lib()
+
+
+def _host(a, pinned):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.pin_memory() if pinned else t.clone()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_cubical_u8_host_buffers(P, oracle, pinned):
+    rng = np.random.default_rng(5)
+    dims = [37, 29, 11]
+    w0 = rng.integers(0, 256, tuple(reversed(dims))).astype(np.uint8)
+    w1 = rng.integers(0, 256, tuple(reversed(dims))).astype(np.uint8)
+    dirs = S.fibonacci_directions(70)
+    T = 45
+    cx = P.CubicalComplex(cuda(w0))
+    out = torch.empty((70, T), dtype=torch.int64)
+    out = out.pin_memory() if pinned else out
+    for w, (lo, hi) in ((w1, (-SQ3, SQ3)), (w0, (math.nan, math.nan)), (w1, (-0.4, 0.7))):
+        got = cx.wect_host(_host(w, pinned), _host(dirs, pinned), T, lo, hi, out=out).numpy()
+        ref = oracle.wect_cubical(dims, w.ravel().astype(np.int64), dirs, T, lo, hi)
+        assert np.array_equal(got, ref), (lo, hi)
+        # the device entry on the same weights gives the same table
+        assert np.array_equal(cx.wect(cuda(dirs), T, lo, hi).cpu().numpy(), ref)
+    cx.device_status()
+
+
+def test_keep_weights_and_unweighted(P, oracle):
+    rng = np.random.default_rng(6)
+    w = rng.integers(0, 256, (23, 41)).astype(np.uint8)
+    dims = [41, 23]
+    dirs = S.circle_directions(40)
+    cx = P.CubicalComplex(cuda(w))
+    got = cx.wect_host(None, _host(dirs, True), 30, -SQ2, SQ2).numpy()
+    assert np.array_equal(got, oracle.wect_cubical(dims, w.ravel().astype(np.int64), dirs, 30, -SQ2, SQ2))
+    one = P.CubicalComplex(None, dims=dims)
+    got = one.wect_host(None, _host(dirs, False), 30, -SQ2, SQ2).numpy()
+    ref = oracle.wect_cubical(dims, np.ones(w.size, np.int64), dirs, 30, -SQ2, SQ2, weighted=False)
+    assert np.array_equal(got, ref)
+
+
+def test_float_weights_host(P, oracle):
+    rng = np.random.default_rng(7)
+    w = rng.uniform(-2.0, 2.0, (19, 33)).astype(np.float32)
+    dims = [33, 19]
+    dirs = S.circle_directions(25)
+    cx = P.CubicalComplex(cuda(np.zeros_like(w)), frac_bits=18)
+    got = cx.wect_host(_host(w, True), _host(dirs, True), 50, -SQ2, SQ2).numpy()
+    ref = oracle.wect_cubical(dims, oracle.to_fixed(w, 18), dirs, 50, -SQ2, SQ2)
+    assert np.array_equal(got, ref)
+    with pytest.raises(ValueError):
+        cx.wect_host(_host(w.astype(np.float64), True), _host(dirs, True), 50, -SQ2, SQ2)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_simplicial_host_buffers(P, oracle, pinned):
+    cx = S.random_simplicial(420, 3, 1200, 700, seed=11)
+    dirs = S.random_directions(50, 3, 12)
+    T = 64
+    h = P.SimplicialComplex(cuda(cx.coords), [cuda(s) for s in cx.simplices], cuda(np.zeros_like(cx.weights)))
+    got = h.wect_host(_host(cx.weights, pinned), _host(dirs, pinned), T, -1.5, 1.5).numpy()
+    vw = cx.weights.astype(np.int64)
+    ref = oracle.wect_simplicial(cx.coords, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), dirs, T, -1.5, 1.5)
+    assert np.array_equal(got, ref)
+
+
+def test_voxel3d_128_host_equals_device(P):
+    """The 128^3 benchmark volume, d = 256, T = 128: the host entry (page-locked buffers, the
+    benchmark's end-to-end call) and the device entry give the same table; its last column is the
+    Euler characteristic of the weighted complex, the same for every direction."""
+    wl = S.voxel3d_128()
+    d, T = len(wl.dirs), wl.T
+    cx = P.CubicalComplex(cuda(np.zeros_like(wl.grid)))
+    got = cx.wect_host(_host(wl.grid, True), _host(wl.dirs, True), T, wl.lo, wl.hi).numpy()
+    ref = cx.wect(cuda(wl.dirs), T, wl.lo, wl.hi).cpu().numpy()
+    assert got.shape == (d, T) and np.array_equal(got, ref)
+    assert np.all(got[:, -1] == got[0, -1])
