@@ -395,7 +395,10 @@ WECT_API int64_t wect_kernel_launch_count(void);
  * events on its stream around its dominant kernel (the stencil or gather scatter kernel, or
  * the replayed batch graph, or the adjoint's kernels).  wect_profile_read synchronises on the
  * recorded events, returns the summed kernel milliseconds and the number of timed launches
- * since the last read, and releases the events.
+ * since the last read, and releases the events.  Outside a stream capture the cubical forward
+ * launches its preparation, stencil kernel and scan as programmatic dependent launches (each
+ * may start while the kernel before it finishes); while the hook is on, the stencil kernel is
+ * launched in plain stream order instead, so that its events bracket all of it.
  */
 WECT_API wect_status wect_profile_enable(int on);
 WECT_API wect_status wect_profile_read(double *kernel_ms, int64_t *launches);

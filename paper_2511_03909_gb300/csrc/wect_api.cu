@@ -638,9 +638,14 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
         CK(cudaMemsetAsync(ws.M.p, 0, sizeof(unsigned long long), st), "memset");
         KL(launch_grid_max_abs(L.n, L.d_grids, dirs, d, ws.M.p, st), "grid_max_abs");
     }
+    // outside a stream capture the preparation, the forward kernel and the scan are programmatic
+    // dependent launches (each starts while the kernel before it finishes)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs), "capture status");
+    const bool pdl = cs == cudaStreamCaptureStatusNone;
     KL(launch_fwd_prep(L.n, dirs, d, T, lo, hi, dflt ? 1 : 0, ws.M.p, ws.range.p, ws.beta.p, ws.perm.p, ws.octb.p,
                        ws.counter.p, L.status, direct ? nullptr : reinterpret_cast<unsigned long long *>(out),
-                       out_rows * T, st, sh.run ? 1 : 0),
+                       out_rows * T, st, sh.run ? 1 : 0, pdl),
        "fwd_prep");
     CubicalFwdArgs a{};
     a.grids = L.d_grids;
@@ -663,10 +668,14 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     a.L0s = sh.L0s;
     a.segmented = L.segmented ? 1 : 0;
     a.Tt = sh.Tt;
+    {
+        // with the profiling hook on, the kernel is launched in plain stream order, so that the
+        // hook's events bracket all of it (an early start would fall before the first event)
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        a.pdl = (pdl && !g_prof_on) ? 1 : 0;
+    }
     const int grid = std::max(1, std::min(sh.grid, n_items));
     {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaStreamIsCapturing(st, &cs);
         g_last_stencil.store(sh.run ? 2 : (sh.gh ? 3 : 1));
         auto launch = [&]() {
             return sh.run ? launch_cubical_run(L.n, a, grid, sh.smem, st)
@@ -681,7 +690,8 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     }
     if (!direct)
         KL(launch_scan_rows_to(reinterpret_cast<unsigned long long *>(out),
-                               reinterpret_cast<unsigned long long *>(final_out ? final_out : out), out_rows, T, st),
+                               reinterpret_cast<unsigned long long *>(final_out ? final_out : out), out_rows, T, st,
+                               pdl && !sh.run),
            "scan_rows");
     return WECT_OK;
 }
@@ -1264,6 +1274,15 @@ extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, co
     if (s) return s;
     cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(c->mu);
+    // the directions: a device copy (every CTA of the forward reads them), made before the
+    // weight conversion, which the forward's preparation overlaps
+    const int64_t nd = (int64_t)d * c->n;
+    CK(c->ws.hdirs.ensure((size_t)nd), "alloc direction copy");
+    const double *dd = static_cast<const double *>(device_alias(dirs));
+    if (dd)
+        KL(launch_copy_f64(dd, c->ws.hdirs.p, nd, st), "copy_f64");
+    else
+        CK(cudaMemcpyAsync(c->ws.hdirs.p, dirs, (size_t)nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy dirs");
     // the weights: read in place by the conversion kernel, or staged when pageable
     if (weights && c->wtype != WECT_W_ONE) {
         const void *wd = device_alias(weights);
@@ -1275,14 +1294,6 @@ extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, co
         }
         if ((s = set_weights_locked(c, wd, st))) return s;
     }
-    // the directions: a device copy (every CTA of the forward reads them)
-    const int64_t nd = (int64_t)d * c->n;
-    CK(c->ws.hdirs.ensure((size_t)nd), "alloc direction copy");
-    const double *dd = static_cast<const double *>(device_alias(dirs));
-    if (dd)
-        KL(launch_copy_f64(dd, c->ws.hdirs.p, nd, st), "copy_f64");
-    else
-        CK(cudaMemcpyAsync(c->ws.hdirs.p, dirs, (size_t)nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy dirs");
     // the difference table on the device; its scan writes out directly when out is mapped
     CK(c->ws.hout.ensure((size_t)d * T), "alloc table");
     int64_t *od = static_cast<int64_t *>(device_alias(out));

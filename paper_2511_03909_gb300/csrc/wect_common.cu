@@ -88,11 +88,16 @@ __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double 
                                 const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
                                 int *counter, int *status, unsigned long long *out, int64_t out_elems, int run_order)
 {
+    // As a programmatic dependent of the weight conversion this grid runs beside it (it reads
+    // none of its output), lets the forward kernel launch at once, and completes only after the
+    // kernel before it (the forward kernel's griddepcontrol.wait then covers both).
+    pdl_trigger();
     if (blockIdx.x == 0) {
         __shared__ int cnt[8], start[9], fill[8];
         if (status)
             for (int i = threadIdx.x; i < d * n; i += blockDim.x)
                 if (!isfinite(dirs[i])) atomicOr(status, kStatusBadIndex);
+        if (use_default) pdl_wait();      // Mbits comes from the kernel before
         range_beta(lo, hi, use_default, Mbits, T, range, beta, threadIdx.x, blockDim.x);
         if (!run_order) octant_sort_block(n, dirs, d, perm, octb, cnt, start, fill);
         if (threadIdx.x == 0) *counter = 0;
@@ -122,6 +127,7 @@ __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double 
             if ((out_elems - head) & 1) out[out_elems - 1] = 0ull;
         }
     }
+    pdl_wait();
 }
 
 // Inclusive prefix sum of each row of an int64 [rows][T] table (Algorithm 1's final cumulative
@@ -129,6 +135,7 @@ __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double 
 // row, 32-wide shuffle scans with a running carry.
 __global__ void scan_rows_kernel(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= rows) return;
@@ -157,6 +164,7 @@ __global__ void __launch_bounds__(1024) scan_rows_block_kernel(const unsigned lo
                                                                int T)
 {
     __shared__ long long wsum[32];
+    pdl_wait();
     const long long *r = reinterpret_cast<const long long *>(src) + (int64_t)blockIdx.x * T;
     long long *o = reinterpret_cast<long long *>(dst) + (int64_t)blockIdx.x * T;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -247,6 +255,7 @@ __global__ void weights_to_fixed_kernel(const void *w, int64_t nv, int frac_bits
 template <int WT>
 __global__ void weights_to_w32_kernel(const void *w, int64_t nv, int frac_bits, int64_t limit, int32_t *out, int *status)
 {
+    pdl_trigger();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
         if (WT == WT_F32) {
             const float x = ((const float *)w)[v];
@@ -266,6 +275,7 @@ __global__ void weights_to_w32_kernel(const void *w, int64_t nv, int frac_bits, 
 // and four 16-byte stores, then the tail.  w is 16-byte aligned.
 __global__ void weights_u8_to_w32_kernel(const uint8_t *__restrict__ w, int64_t nv, int32_t *__restrict__ out)
 {
+    pdl_trigger();          // the forward's preparation reads none of this
     const int64_t n16 = nv >> 4, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
         const uint4 x = __ldg(reinterpret_cast<const uint4 *>(w) + i);
@@ -378,15 +388,14 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
                             int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
-                            int run_order)
+                            int run_order, bool pdl)
 {
     if (out && (reinterpret_cast<uintptr_t>(out) & 7u)) return cudaErrorMisalignedAddress;   // int64 alignment
     int64_t work = out ? (out_elems / 2 + 255) / 256 : 1;
     if (run_order) work = std::max<int64_t>(work, (d + 255) / 256);
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, 152 * 4));
-    fwd_prep_kernel<<<g, 256, 0, st>>>(n, dirs, d, T, lo, hi, use_default, Mbits, range, beta, perm, octb, counter,
-                                       status, out, out_elems, run_order);
-    return cudaGetLastError();
+    return launch_kernel(fwd_prep_kernel, dim3(g), dim3(256), 0, st, pdl, n, dirs, d, T, lo, hi, use_default, Mbits, range,
+                         beta, perm, octb, counter, status, out, out_elems, run_order);
 }
 
 cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st)
@@ -396,18 +405,17 @@ cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int 
 }
 
 cudaError_t launch_scan_rows_to(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T,
-                                cudaStream_t st)
+                                cudaStream_t st, bool pdl)
 {
     if (rows <= 0) return cudaSuccess;
     if (T >= 1024 && rows <= 65535) {
         // a block of up to 1024 threads per row, about 8 entries per thread
         const int threads = std::min(1024, ((T + 7) / 8 + 31) / 32 * 32);
-        scan_rows_block_kernel<<<(unsigned)rows, threads, 0, st>>>(src, dst, T);
-        return cudaGetLastError();
+        return launch_kernel(scan_rows_block_kernel, dim3((unsigned)rows), dim3(threads), 0, st, pdl, src, dst, T);
     }
     const int wpb = 8;
-    scan_rows_kernel<<<(unsigned)((rows + wpb - 1) / wpb), wpb * 32, 0, st>>>(src, dst, rows, T);
-    return cudaGetLastError();
+    return launch_kernel(scan_rows_kernel, dim3((unsigned)((rows + wpb - 1) / wpb)), dim3(wpb * 32), 0, st, pdl, src, dst,
+                         rows, T);
 }
 
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st)

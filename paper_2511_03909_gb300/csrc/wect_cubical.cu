@@ -340,6 +340,10 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     const int flushTiles = (int)((dynamic_smem_bytes() - (uint32_t)(NSPLIT * histWords) * 4u) / (NSPLIT * 32u * 33u * 4u));
 
     for (int i = tid; i < NSPLIT * histWords; i += blockDim.x) hist[i] = 0;
+    // launched as a programmatic dependent: the set-up above overlapped the preparation kernel;
+    // its results (and the weights) are read only from here on, and the scan may launch
+    pdl_wait();
+    pdl_trigger();
 
     for (;;) {
         __syncthreads();
@@ -515,8 +519,7 @@ static cudaError_t launch_fwd_s(const CubicalFwdArgs &a, int grid, size_t smem, 
     }
     if (!launch) return cudaSuccess;
     const int threads = (a.threads > 0 && a.threads <= kFwdThreads) ? a.threads : kFwdThreads;
-    cubical_fwd_kernel<N, NSPLIT, DPL, GH, GEN><<<grid, threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(cubical_fwd_kernel<N, NSPLIT, DPL, GH, GEN>, dim3(grid), dim3(threads), smem, st, a.pdl != 0, a);
 }
 
 // The general instance (segments of long rows, threshold tiles) only when the launch needs it;

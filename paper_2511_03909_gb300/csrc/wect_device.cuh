@@ -270,6 +270,19 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Programmatic dependent launch: let the next kernel of the stream (launched with the
+// programmatic-serialization attribute) start, and wait until the kernels this grid depends on
+// have completed with their memory visible.  Both are no-ops without such a launch.
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Bytes of dynamic shared memory the CTA was launched with.
 __device__ __forceinline__ uint32_t dynamic_smem_bytes()
 {

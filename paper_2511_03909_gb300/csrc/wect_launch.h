@@ -30,7 +30,29 @@ struct CubicalFwdArgs {
     int segmented;                // some grid walks its rows in segments (GridDesc::seg, nseg)
     int Tt;                       // > 0: threshold tiles of Tt bins (WorkItem::tt); the shared
                                   // histogram then holds Tt + 2 rows (a discard row on each side)
+    int pdl;                      // launch as a programmatic dependent of the preceding kernel
 };
+
+// Launch k<<<g, b, smem, st>>>(args...), as a programmatic dependent launch when pdl is set: the
+// grid may start once every CTA of the preceding kernel in the stream has signalled
+// (griddepcontrol.launch_dependents) or exited, and it reads that kernel's results only after
+// its own griddepcontrol.wait.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st, bool pdl,
+                                 Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 struct CubicalBwdArgs {
     const GridDesc *grids;
@@ -189,11 +211,11 @@ cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int 
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
                             int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
-                            int run_order = 0);
+                            int run_order = 0, bool pdl = false);
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
 // The same scan from src into dst (dst may be mapped pinned host memory; src == dst is in place).
 cudaError_t launch_scan_rows_to(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T,
-                                cudaStream_t st);
+                                cudaStream_t st, bool pdl = false);
 cudaError_t launch_copy_f64(const double *src, double *dst, int64_t n, cudaStream_t st);
 cudaError_t launch_suffix_rows(const int64_t *in, int64_t *out, int64_t rows, int T, long long smax, int *status,
                                cudaStream_t st);
