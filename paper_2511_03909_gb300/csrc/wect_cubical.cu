@@ -434,7 +434,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
 #pragma unroll
                 for (int o = 0; o < NOCT; ++o) {
                     const int32_t v = c[o];
-                    if ((int64_t)v > P.climit || (int64_t)v < -P.climit) atomicOr(g.status, kStatusOverflow);
                     if (NSPLIT == 1) {
                         crow[o * CP + i0] = v;
                     } else {

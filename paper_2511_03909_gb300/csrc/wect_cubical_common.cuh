@@ -9,8 +9,17 @@ namespace wect {
 // ------------------------------------------------------------------ octant contributions
 
 // c_o(v) for every octant o from the int32 fixed-point weights of v's 3^n neighbourhood (the
-// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set).  ld(dx, dy, dz)
-// returns the weight of vertex (i0 + dx, i1 + dy, i2 + dz); it is called only inside the grid.
+// accumulator modes bound 2^n max|w| below 2^31, checked when the weights are set, so |c_o| fits
+// int32).  ld(dx, dy, dz) returns the weight of vertex (i0 + dx, i1 + dy, i2 + dz); it is called
+// only inside the grid.
+//
+// c_o(v) = sum over the axis subsets e of (-1)^|e| w(cell spanned by v and its neighbours on the
+// sides of o along the axes in e), the cell weight being the max over its vertices.  Vertices
+// outside the grid stand in with weight S = 2^31 - 1, so the box maximum of every cell that leaves
+// the grid is S, and the sum runs over all 2^n subsets without masks, in wrapping 32-bit
+// arithmetic.  The S terms cancel: their signs sum to -[no side of o lies inside the grid] (the
+// signed count of the subsets that meet the outside axes), so the plain sum is exact except at a
+// grid corner of o, where the only cell is v itself and c_o = w(v).
 template <int N, class Load>
 __device__ __forceinline__ void octant_contribs_with(Load ld, int L0, int L1, int L2, int i0, int i1, int i2,
                                                      int32_t *c /* [1 << N] */)
@@ -18,6 +27,7 @@ __device__ __forceinline__ void octant_contribs_with(Load ld, int L0, int L1, in
     constexpr int NOCT = 1 << N;
     constexpr int NY = (N >= 2) ? 3 : 1;
     constexpr int NZ = (N >= 3) ? 3 : 1;
+    constexpr int32_t S = 0x7fffffff;
     const bool ok0[3] = {i0 > 0, true, i0 < L0 - 1};
     const bool ok1[3] = {i1 > 0, true, i1 < L1 - 1};
     const bool ok2[3] = {i2 > 0, true, i2 < L2 - 1};
@@ -33,7 +43,7 @@ __device__ __forceinline__ void octant_contribs_with(Load ld, int L0, int L1, in
             for (int x = 0; x < 3; ++x) {
                 const int dy = (N >= 2) ? y - 1 : 0, dz = (N >= 3) ? z - 1 : 0;
                 const bool ok = ok0[x] && (N < 2 || ok1[y]) && (N < 3 || ok2[z]);
-                w[x] = ok ? ld(x - 1, dy, dz) : 0;
+                w[x] = ok ? ld(x - 1, dy, dz) : S;
             }
             A[z][y][0] = max(w[0], w[1]);
             A[z][y][1] = w[1];
@@ -59,25 +69,26 @@ __device__ __forceinline__ void octant_contribs_with(Load ld, int L0, int L1, in
                 if (NZ > 2) A[2][y][x] = max(a1, a2);
             }
     }
+    const int32_t wv = A[NZ / 2][NY / 2][1];
 #pragma unroll
     for (int o = 0; o < NOCT; ++o) {
-        int32_t acc = 0;
+        uint32_t acc = 0;
+        bool inside = false;                 // some side of o lies inside the grid
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const int side = ((o >> a) & 1) ? 0 : 2;     // sign corner at the upper end: the cells reach back
+            inside = inside || (a == 0 ? ok0[side] : (a == 1 ? ok1[side] : ok2[side]));
+        }
 #pragma unroll
         for (int e = 0; e < NOCT; ++e) {
             int idx[3] = {1, 1, 1};
-            bool ok = true;
 #pragma unroll
-            for (int a = 0; a < N; ++a) {
-                if ((e >> a) & 1) {
-                    const bool up = (o >> a) & 1;            // sign corner is the upper end: the cell reaches back
-                    idx[a] = up ? 0 : 2;
-                    ok = ok && (a == 0 ? ok0[idx[a]] : (a == 1 ? ok1[idx[a]] : ok2[idx[a]]));
-                }
-            }
-            const int32_t wb = A[N >= 3 ? idx[2] : 0][N >= 2 ? idx[1] : 0][idx[0]];
-            if (ok) acc += (__popc(e) & 1) ? -wb : wb;
+            for (int a = 0; a < N; ++a)
+                if ((e >> a) & 1) idx[a] = ((o >> a) & 1) ? 0 : 2;
+            const uint32_t wb = (uint32_t)A[N >= 3 ? idx[2] : 0][N >= 2 ? idx[1] : 0][idx[0]];
+            acc = (__popc(e) & 1) ? acc - wb : acc + wb;
         }
-        c[o] = acc;
+        c[o] = inside ? (int32_t)acc : wv;
     }
 }
 

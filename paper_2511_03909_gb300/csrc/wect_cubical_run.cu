@@ -140,7 +140,6 @@ __global__ void __launch_bounds__(kRunThreads, 1) cubical_run_kernel(const Cubic
 #pragma unroll
                 for (int o = 0; o < NOCT; ++o) {
                     const int32_t v = c[o];
-                    if ((int64_t)v > P.climit || (int64_t)v < -P.climit) atomicOr(g.status, kStatusOverflow);
                     crow[o * CP + i0] = v;
                 }
             }
