@@ -1171,11 +1171,18 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
     CK(cudaMemsetAsync(out, 0, (size_t)d * T * sizeof(int64_t), st), "memset");
     const int grid = sm_count();
     const bool staged_ok = simplex_fwd_staged_smem(c->nsplit, T, Dt) <= smem_optin() - 1024;
+    // outside a stream capture the gathers after the first are programmatic dependent launches
+    // (each clears its histogram while the one before finishes)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs), "capture status");
+    bool pdl = false;
     ProfScope prof(st);
     for (int dt = 0; dt * Dt < d; ++dt) {
         for (int i = 0; i <= c->max_dim; ++i) {
             if (i > 0 && c->counts[i] == 0) continue;
             SimplexFwdArgs a{};
+            a.pdl = pdl ? 1 : 0;
+            pdl = cs == cudaStreamCaptureStatusNone;
             a.simp = (i == 0) ? nullptr : c->d_simp[i];
             a.sw = c->d_sw[i];
             a.swp = c->d_swp[i];
@@ -1225,7 +1232,7 @@ static wect_status simplicial_compute(wect_complex c, const double *dirs, int d,
         }
     }
     KL(launch_scan_rows_to(reinterpret_cast<unsigned long long *>(out),
-                           reinterpret_cast<unsigned long long *>(final_out ? final_out : out), d, T, st),
+                           reinterpret_cast<unsigned long long *>(final_out ? final_out : out), d, T, st, pdl),
        "scan_rows");
     return WECT_OK;
 }

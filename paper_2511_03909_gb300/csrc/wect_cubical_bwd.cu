@@ -436,17 +436,22 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
     }
     const int32_t *wp = g.w + v;
     const int32_t wv = __ldg(wp);
-    // neighbour offsets (flat, int32), in-bounds mask and "beats v" mask over the 3^n neighbourhood
+    // neighbour offsets (flat, int32) and the "beats v" mask over the 3^n neighbourhood; a
+    // position outside the grid counts as beating v, so that no cell holding it is v's
+    const bool ox[3] = {i0 > 0, true, i0 < L0 - 1};
+    const bool oy[3] = {i1 > 0, true, i1 < L1 - 1};
+    const bool oz[3] = {i2 > 0, true, i2 < L2 - 1};
     int off[NB];
-    uint32_t okm = 0, beat = 0;
+    uint32_t beat = 0;
 #pragma unroll
     for (int t = 0; t < NB; ++t) {
         const int dx = t % 3 - 1, dy = (N >= 2) ? (t / 3) % 3 - 1 : 0, dz = (N >= 3) ? t / 9 - 1 : 0;
         off[t] = dx + L0 * (dy + L1 * dz);
-        const bool ok = i0 + dx >= 0 && i0 + dx < L0 && i1 + dy >= 0 && i1 + dy < L1 && i2 + dz >= 0 && i2 + dz < L2;
-        if (ok) {
-            okm |= 1u << t;
-            if (t != CENTER) {
+        const bool ok = ox[dx + 1] && oy[dy + 1] && oz[dz + 1];
+        if (t != CENTER) {
+            if (!ok) {
+                beat |= 1u << t;
+            } else {
                 const int32_t wu = __ldg(wp + off[t]);
                 // u's flat index is below v's iff its offset is lexicographically negative
                 const bool below = (dz < 0) || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
@@ -454,12 +459,11 @@ __global__ void __launch_bounds__(256) cubical_bwd_route_kernel(const CubicalBwd
             }
         }
     }
-    // cells v takes: in bounds (the far corner v + e is) and beaten nowhere
+    // cells v takes: beaten nowhere (a cell leaving the grid holds a position that beats v)
     uint32_t A = 0;
 #pragma unroll
     for (int t = 0; t < NB; ++t)
-        if ((okm >> t) & 1u)
-            if ((beat & route_cell_mask(N, t)) == 0) A |= 1u << t;
+        if ((beat & route_cell_mask(N, t)) == 0) A |= 1u << t;
     // K = #(A & even & class) - #(A & odd & class) = #(X & class) - #(odd & class) with
     // X = A ^ odd: one mask and one popcount per coefficient, the second count a constant
     const uint32_t X = A ^ route_odd_mask(N);

@@ -100,6 +100,7 @@ struct SimplexFwdArgs {
     const int32_t *cnu;           // [nchunks] distinct vertices of each chunk, -1 above kWinRows
     int64_t nchunks;
     int flush_every;              // chunks between histogram flushes
+    int pdl;                      // launch as a programmatic dependent of the preceding kernel
 };
 
 // Staged simplex chunks: kChunkSlots vertex slots per chunk (kChunkSlots / m simplices), and a

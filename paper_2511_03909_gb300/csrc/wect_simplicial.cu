@@ -293,6 +293,8 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_kernel(const S
         for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
         __syncthreads();
     }
+    pdl_wait();             // a programmatic dependent: the bins and the table from here on
+    pdl_trigger();
     const uint16_t *bins = P.bins + lane;
     const int64_t nchunks = (P.k + P.chunk - 1) / P.chunk;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -345,6 +347,8 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) vertex_scatter_kernel(cons
     const uint32_t HOFF = (uint32_t)T * 128u;
     for (int i = threadIdx.x; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
     __syncthreads();
+    pdl_wait();             // the previous tile's gathers have read the bins this kernel rewrites
+    pdl_trigger();
     const int p = P.dtile * 32 + lane;
     const bool act = p < d;
     const int pc = act ? p : d - 1;
@@ -565,6 +569,8 @@ __global__ void __launch_bounds__(kSimplexThreads, 1) simplex_fwd_staged_kernel(
     const uint32_t histLane = histAddr + (uint32_t)lane * 4u;
     const uint32_t HOFF = (uint32_t)T * 128u;
     for (int i = tid; i < NSPLIT * T * 32; i += blockDim.x) hist[i] = 0;
+    pdl_wait();             // a programmatic dependent: the tile's vertex bins from here on
+    pdl_trigger();
     const int64_t cb = P.nchunks * blockIdx.x / gridDim.x, ce = P.nchunks * (blockIdx.x + 1) / gridDim.x;
 
     // window rows of this thread's copies of chunk c (vertex id, or -1) and the chunk's width u
@@ -937,7 +943,8 @@ cudaError_t launch_vertex_scatter(int n, int nsplit, const SimplexFwdArgs &a, co
     do {                                                                                                             \
         e = cudaFuncSetAttribute(vertex_scatter_kernel<NN, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e == cudaSuccess)                                                                                        \
-            vertex_scatter_kernel<NN, SS><<<grid, kSimplexThreads, sm, st>>>(a, coords, xf, nv, dirs, tab, beta, bins); \
+            e = launch_kernel(vertex_scatter_kernel<NN, SS>, dim3(grid), dim3(kSimplexThreads), sm, st, a.pdl != 0, a, \
+                              coords, xf, nv, dirs, tab, beta, bins);                                                \
     } while (0)
     if (nsplit == 1) {
         if (n == 1) VS(1, 1); else if (n == 2) VS(2, 1); else if (n == 3) VS(3, 1); else VS(4, 1);
@@ -960,7 +967,9 @@ static cudaError_t launch_simplex_fwd_s(const SimplexFwdArgs &a, int grid, cudaS
     do {                                                                                                            \
         e = cudaFuncSetAttribute(simplex_fwd_kernel<NSPLIT, MM, GH>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                  (int)sm);                                                                          \
-        if (e == cudaSuccess) simplex_fwd_kernel<NSPLIT, MM, GH><<<grid, kSimplexThreads, sm, st>>>(a);            \
+        if (e == cudaSuccess)                                                                                       \
+            e = launch_kernel(simplex_fwd_kernel<NSPLIT, MM, GH>, dim3(grid), dim3(kSimplexThreads), sm, st,       \
+                              a.pdl != 0, a);                                                                        \
     } while (0)
     switch (a.m) {
     case 1: SF(1); break;
@@ -1016,7 +1025,9 @@ static cudaError_t launch_simplex_fwd_staged_s(const SimplexFwdArgs &a, int grid
     do {                                                                                                              \
         e = cudaFuncSetAttribute(simplex_fwd_staged_kernel<NSPLIT, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)sm);                                                                            \
-        if (e == cudaSuccess) simplex_fwd_staged_kernel<NSPLIT, MM><<<grid, kSimplexThreads, sm, st>>>(a);           \
+        if (e == cudaSuccess)                                                                                         \
+            e = launch_kernel(simplex_fwd_staged_kernel<NSPLIT, MM>, dim3(grid), dim3(kSimplexThreads), sm, st,      \
+                              a.pdl != 0, a);                                                                          \
     } while (0)
     switch (a.m) {
     case 2: SS(2); break;
