@@ -93,3 +93,51 @@ def test_voxel3d_128_host_equals_device(P):
     ref = cx.wect(cuda(wl.dirs), T, wl.lo, wl.hi).cpu().numpy()
     assert got.shape == (d, T) and np.array_equal(got, ref)
     assert np.all(got[:, -1] == got[0, -1])
+
+
+def test_back_to_back_calls_without_synchronisation(P, oracle):
+    """Consecutive set_weights + wect calls (and host-buffer calls) queued on one stream with no
+    host synchronisation in between: each call's programmatic launches must see its own weights
+    and must not disturb the previous call's table."""
+    rng = np.random.default_rng(21)
+    dims = [45, 33, 7]
+    ws = [rng.integers(0, 256, tuple(reversed(dims))).astype(np.uint8) for _ in range(6)]
+    dirs = S.fibonacci_directions(96)
+    T, lo, hi = 64, -SQ3, SQ3
+    cx = P.CubicalComplex(cuda(ws[0]))
+    dd = cuda(dirs)
+    outs = [torch.empty((96, T), dtype=torch.int64, device=dd.device) for _ in ws]
+    wd = [cuda(w) for w in ws]
+    for w, o in zip(wd, outs):
+        cx.set_weights(w)
+        cx.wect(dd, T, lo, hi, out=o)
+    hosts = [torch.empty((96, T), dtype=torch.int64).pin_memory() for _ in ws]
+    wh = [_host(w, True) for w in ws]
+    dh = _host(dirs, True)
+    for w, o in zip(wh, hosts):
+        cx.wect_host(w, dh, T, lo, hi, out=o, sync=False)
+    torch.cuda.synchronize()
+    for w, o, h in zip(ws, outs, hosts):
+        ref = oracle.wect_cubical(dims, w.ravel().astype(np.int64), dirs, T, lo, hi)
+        assert np.array_equal(o.cpu().numpy(), ref)
+        assert np.array_equal(h.numpy(), ref)
+
+
+def test_simplicial_back_to_back_calls(P, oracle):
+    """The gathers' programmatic launches over consecutive calls with new weights."""
+    cx = S.random_simplicial(350, 2, 900, 500, seed=23)
+    dirs = S.random_directions(70, 2, 24)
+    rng = np.random.default_rng(25)
+    wlist = [rng.integers(0, 256, cx.nv).astype(np.uint8) for _ in range(4)]
+    h = P.SimplicialComplex(cuda(cx.coords), [cuda(s) for s in cx.simplices], cuda(wlist[0]))
+    dd = cuda(dirs)
+    outs = []
+    for w in wlist:
+        h.set_weights(cuda(w))
+        outs.append(h.wect(dd, 50, -1.5, 1.5))
+    torch.cuda.synchronize()
+    for w, o in zip(wlist, outs):
+        vw = w.astype(np.int64)
+        ref = oracle.wect_simplicial(cx.coords, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), dirs, 50,
+                                     -1.5, 1.5)
+        assert np.array_equal(o.cpu().numpy(), ref)
