@@ -141,3 +141,21 @@ def test_simplicial_back_to_back_calls(P, oracle):
         ref = oracle.wect_simplicial(cx.coords, cx.simplices, oracle.simplicial_weights(cx.simplices, vw), dirs, 50,
                                      -1.5, 1.5)
         assert np.array_equal(o.cpu().numpy(), ref)
+
+
+def test_device_pointers_accepted(P, oracle):
+    """The C entry takes device memory too (used in place): device weights, directions and table."""
+    import ctypes as C
+
+    rng = np.random.default_rng(31)
+    dims = [40, 18]
+    w = rng.integers(0, 256, tuple(reversed(dims))).astype(np.uint8)
+    dirs = S.circle_directions(36)
+    cx = P.CubicalComplex(cuda(np.zeros_like(w)))
+    wd, dd = cuda(w), cuda(dirs)
+    out = torch.empty((36, 40), dtype=torch.int64, device=dd.device)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert P.load().wect_compute_host(cx.handle, C.c_void_p(wd.data_ptr()), C.c_void_p(dd.data_ptr()), 36, 40,
+                                      -SQ2, SQ2, C.c_void_p(out.data_ptr()), st) == 0
+    ref = oracle.wect_cubical(dims, w.ravel().astype(np.int64), dirs, 40, -SQ2, SQ2)
+    assert np.array_equal(out.cpu().numpy(), ref)
