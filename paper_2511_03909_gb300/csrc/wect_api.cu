@@ -1254,8 +1254,9 @@ extern "C" wect_status wect_compute(wect_complex c, const double *dirs, int d, i
 
 // The device address of a caller buffer: device memory of the current device and managed memory
 // as they are, page-locked host memory through its mapping into the device's address space
-// (kernels read and write it over the host link); null for pageable host memory, which is
-// copied instead.
+// (kernels read and write it over the host link); null for pageable host memory (and memory of
+// another device), which is copied instead (cudaMemcpyDefault: the unified address space tells
+// the direction).
 static void *device_alias(const void *p)
 {
     cudaPointerAttributes a{};
@@ -1289,14 +1290,14 @@ extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, co
     if (dd)
         KL(launch_copy_f64(dd, c->ws.hdirs.p, nd, st), "copy_f64");
     else
-        CK(cudaMemcpyAsync(c->ws.hdirs.p, dirs, (size_t)nd * sizeof(double), cudaMemcpyHostToDevice, st), "copy dirs");
+        CK(cudaMemcpyAsync(c->ws.hdirs.p, dirs, (size_t)nd * sizeof(double), cudaMemcpyDefault, st), "copy dirs");
     // the weights: read in place by the conversion kernel, or staged when pageable
     if (weights && c->wtype != WECT_W_ONE) {
         const void *wd = device_alias(weights);
         if (!wd) {
             const size_t bytes = (size_t)c->nv * c->wbytes;
             CK(c->ws.hw.ensure(bytes), "alloc weight staging");
-            CK(cudaMemcpyAsync(c->ws.hw.p, weights, bytes, cudaMemcpyHostToDevice, st), "copy weights");
+            CK(cudaMemcpyAsync(c->ws.hw.p, weights, bytes, cudaMemcpyDefault, st), "copy weights");
             wd = c->ws.hw.p;
         }
         if ((s = set_weights_locked(c, wd, st))) return s;
@@ -1312,7 +1313,7 @@ extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, co
     }
     if (s) return s;
     if (!od)
-        CK(cudaMemcpyAsync(out, c->ws.hout.p, (size_t)d * T * sizeof(int64_t), cudaMemcpyDeviceToHost, st), "copy table");
+        CK(cudaMemcpyAsync(out, c->ws.hout.p, (size_t)d * T * sizeof(int64_t), cudaMemcpyDefault, st), "copy table");
     return WECT_OK;
 }
 
