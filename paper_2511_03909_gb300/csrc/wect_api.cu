@@ -631,7 +631,8 @@ struct CubLaunch {
 // [scan].  items must be uploaded in ws->items already.
 static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, int n_items, bool direct,
                                        const double *dirs, int d, int T, double lo, double hi, bool dflt,
-                                       int64_t out_rows, int64_t *out, cudaStream_t st, int64_t *final_out = nullptr)
+                                       int64_t out_rows, int64_t *out, cudaStream_t st, int64_t *final_out = nullptr,
+                                       bool prep_early = false)
 {
     Workspace &ws = *L.ws;
     if (dflt) {
@@ -645,7 +646,7 @@ static wect_status enqueue_cubical_fwd(const CubLaunch &L, const CubShape &sh, i
     const bool pdl = cs == cudaStreamCaptureStatusNone;
     KL(launch_fwd_prep(L.n, dirs, d, T, lo, hi, dflt ? 1 : 0, ws.M.p, ws.range.p, ws.beta.p, ws.perm.p, ws.octb.p,
                        ws.counter.p, L.status, direct ? nullptr : reinterpret_cast<unsigned long long *>(out),
-                       out_rows * T, st, sh.run ? 1 : 0, pdl),
+                       out_rows * T, st, sh.run ? 1 : 0, pdl, pdl && prep_early && !dflt),
        "fwd_prep");
     CubicalFwdArgs a{};
     a.grids = L.d_grids;
@@ -1110,8 +1111,9 @@ static wect_status dirs_check(wect_complex c, const double *dirs, int d, cudaStr
 
 // out: the int64 [d][T] table the forward accumulates into; final_out (null: out) receives its
 // scan (simplicial_compute likewise).
+// prep_early: the kernel enqueued just before is this call's own weight conversion.
 static wect_status cubical_compute(wect_complex c, const double *dirs, int d, int T, double lo, double hi, int64_t *out,
-                                   cudaStream_t st, int64_t *final_out = nullptr)
+                                   cudaStream_t st, int64_t *final_out = nullptr, bool prep_early = false)
 {
     CubShape sh;
     GridDesc gd{};
@@ -1137,7 +1139,7 @@ static wect_status cubical_compute(wect_complex c, const double *dirs, int d, in
     CubLaunch L{c->n, c->nsplit, c->wtype, c->frac_bits, c->kflush, ul, c->climit, c->d_grid, &c->ws, c->d_status,
                 gd.nseg > 1};
     return enqueue_cubical_fwd(L, sh, c->ws.n_items, direct, dirs, d, T, lo, hi, range_is_default(lo, hi), d, out, st,
-                               final_out);
+                               final_out, prep_early);
 }
 
 static wect_status simplicial_range(wect_complex c, const double *dirs, int d, int T, double lo, double hi, cudaStream_t st)
@@ -1306,7 +1308,8 @@ extern "C" wect_status wect_compute_host(wect_complex c, const void *weights, co
     CK(c->ws.hout.ensure((size_t)d * T), "alloc table");
     int64_t *od = static_cast<int64_t *>(device_alias(out));
     if (c->kind == 0) {
-        s = cubical_compute(c, c->ws.hdirs.p, d, T, lo, hi, c->ws.hout.p, st, od);
+        // (the kernel just before is this call's weight conversion or direction copy)
+        s = cubical_compute(c, c->ws.hdirs.p, d, T, lo, hi, c->ws.hout.p, st, od, true);
     } else {
         if ((s = dirs_check(c, c->ws.hdirs.p, d, st))) return s;
         s = simplicial_compute(c, c->ws.hdirs.p, d, T, lo, hi, c->ws.hout.p, st, od);

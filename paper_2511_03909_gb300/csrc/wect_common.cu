@@ -86,12 +86,16 @@ __device__ __forceinline__ double run_key(const double *dirs, int n, int p)
 
 __global__ void fwd_prep_kernel(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                                 const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
-                                int *counter, int *status, unsigned long long *out, int64_t out_elems, int run_order)
+                                int *counter, int *status, unsigned long long *out, int64_t out_elems, int run_order,
+                                int early)
 {
-    // As a programmatic dependent of the weight conversion this grid runs beside it (it reads
-    // none of its output), lets the forward kernel launch at once, and completes only after the
-    // kernel before it (the forward kernel's griddepcontrol.wait then covers both).
+    // A programmatic dependent: the forward kernel may launch at once.  When the kernel before is
+    // known to be the library's weight conversion (early), this grid runs beside it, since it
+    // reads none of its output, and waits for it only before exiting, so that the forward
+    // kernel's griddepcontrol.wait covers both.  Otherwise the kernel before may be the caller's,
+    // which may have written the directions or still read the table: wait first.
     pdl_trigger();
+    if (!early) pdl_wait();
     if (blockIdx.x == 0) {
         __shared__ int cnt[8], start[9], fill[8];
         if (status)
@@ -388,14 +392,14 @@ cudaError_t launch_setup_range_beta(double lo, double hi, int use_default, const
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
                             int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
-                            int run_order, bool pdl)
+                            int run_order, bool pdl, bool early)
 {
     if (out && (reinterpret_cast<uintptr_t>(out) & 7u)) return cudaErrorMisalignedAddress;   // int64 alignment
     int64_t work = out ? (out_elems / 2 + 255) / 256 : 1;
     if (run_order) work = std::max<int64_t>(work, (d + 255) / 256);
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, 152 * 4));
     return launch_kernel(fwd_prep_kernel, dim3(g), dim3(256), 0, st, pdl, n, dirs, d, T, lo, hi, use_default, Mbits, range,
-                         beta, perm, octb, counter, status, out, out_elems, run_order);
+                         beta, perm, octb, counter, status, out, out_elems, run_order, early ? 1 : 0);
 }
 
 cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int *octb, cudaStream_t st)

@@ -209,10 +209,12 @@ cudaError_t launch_octant_sort(int n, const double *dirs, int d, int *perm, int 
 // octant grouping, work-queue head, and (out non-null) a cleared output table of out_elems int64.
 // run_order: perm lists the directions by increasing |s_0| (the run kernel's order) instead of
 // grouped by octant (octb is then not written).
+// pdl: a programmatic dependent launch; early (with pdl): the kernel before is the library's weight
+// conversion, which the preparation may overlap (it reads its own inputs before waiting).
 cudaError_t launch_fwd_prep(int n, const double *dirs, int d, int T, double lo, double hi, int use_default,
                             const unsigned long long *Mbits, double *range, double *beta, int *perm, int *octb,
                             int *counter, int *status, unsigned long long *out, int64_t out_elems, cudaStream_t st,
-                            int run_order = 0, bool pdl = false);
+                            int run_order = 0, bool pdl = false, bool early = false);
 cudaError_t launch_scan_rows(unsigned long long *data, int64_t rows, int T, cudaStream_t st);
 // The same scan from src into dst (dst may be mapped pinned host memory; src == dst is in place).
 cudaError_t launch_scan_rows_to(const unsigned long long *src, unsigned long long *dst, int64_t rows, int T,
