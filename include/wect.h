@@ -28,6 +28,12 @@
  *     be freed after they return.  Outputs must not alias inputs.
  *   - Every compute call is asynchronous and ordered on the given stream (a cudaStream_t;
  *     NULL is the legacy default stream).  Create calls synchronise the stream once.
+ *     Outside a stream capture some kernels of a call are programmatic dependent launches of
+ *     the call's own kernels; the first kernel of a call waits for everything before it, and
+ *     the last one signals completion only when it ends.  The weight conversion of
+ *     wect_complex_set_weights signals dependents at its start: a caller's kernel launched
+ *     right after it as a programmatic dependent must wait (cudaGridDependencySynchronize)
+ *     before touching the weights it was given.
  *   - Every call returns a wect_status; no C++ exception crosses the ABI.  On an argument
  *     error nothing is launched and outputs are untouched.  wect_last_error() returns a
  *     thread-local description of the last failure.

@@ -319,7 +319,6 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     uint32_t *wq = reinterpret_cast<uint32_t *>(reinterpret_cast<int32_t *>(dirf + Dt) + RG * nbuf * rowbuf) + wid * 32;
     const uint32_t histAddr = smem_addr(hist);
     const uint32_t HOFF = (uint32_t)histWords * 4u;
-    const double lo = P.range[0], hi = P.range[1], step = P.range[2];
     // TMA staging of the neighbouring rows: two boxes per row group, each NROWS rows of up to
     // L0s int32 (128-byte aligned), filled by the group's first thread one row ahead
     const uint32_t rawEnd = smem_addr(wq - wid * 32 + nwarps * 32);       // end of the fix-up queues
@@ -340,10 +339,14 @@ __global__ void __launch_bounds__(kFwdThreads, 1) cubical_fwd_kernel(const Cubic
     const int flushTiles = (int)((dynamic_smem_bytes() - (uint32_t)(NSPLIT * histWords) * 4u) / (NSPLIT * 32u * 33u * 4u));
 
     for (int i = tid; i < NSPLIT * histWords; i += blockDim.x) hist[i] = 0;
-    // launched as a programmatic dependent: the set-up above overlapped the preparation kernel;
-    // its results (and the weights) are read only from here on, and the scan may launch
+    // launched as a programmatic dependent: the set-up above (shared memory only) overlapped the
+    // preparation kernel; global memory is touched only from here on (its results and the
+    // weights), and the scan may launch (items that store the final table themselves make this
+    // the call's last kernel: no early signal)
     pdl_wait();
-    pdl_trigger();
+    if (!P.direct) pdl_trigger();
+    // the range comes from the preparation kernel: read only after the wait
+    const double lo = P.range[0], hi = P.range[1], step = P.range[2];
 
     for (;;) {
         __syncthreads();
